@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Throughput of the SLDG Strang step on GB300: one JSON line on stdout.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision fp64|fp32]
+
+A step is one Strang step of the whole hot path (x1, x2 half drifts, rho,
+Poisson, v1, v2 kicks, x1, x2 half drifts) over the synthetic initial value
+of the workload (default: nonlinear Landau damping, 64^4 cells, degree 2,
+1.36e9 nodal values, FP64).  ``value`` is dof-updates per second over the
+whole job with f resident in HBM; ``e2e`` is the same metric through the C
+ABI with f uploaded from pinned host memory and W read back every step.
+With torchrun (N > 1) every rank runs an independent replica (the path
+needs no exchange on one GPU): value is the sum over ranks, timed by the
+slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4D SLDG dof-updates/s & HBM GB/s (FP64 vs FP32); adjoint/forward step ratio"
+UNIT = "dof-updates/s"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+FP64_FMA_PER_CLK_SM = 2   # FP64 FMA units per SM of GB300 (1.25 TFLOP/s nominal)
+SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="nonlinear_landau_64")
+    p.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
+    p.add_argument("--no-extras", action="store_true", help="skip the fp32 and adjoint lines")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and committed ncu traffic
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def csrc_sha1():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1803_02143_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(key):
+    """DRAM bytes per launch of a kernel from a committed ncu capture, or None
+    when the kernel sources changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(key)
+    if not e or e.get("csrc_sha1") != csrc_sha1():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline on a bounded slab of the workload
+# ---------------------------------------------------------------------------
+def oracle_slab(w, vcells=16):
+    """Same x-grid and degree, v reduced to vcells^2 cells: per-dof work of
+    the sweeps is unchanged (same line lengths along x, same degree)."""
+    import oracle as orc
+
+    c = w.cfg
+    nc = (c.ncell[0], c.ncell[1], min(c.ncell[2], vcells), min(c.ncell[3], vcells))
+    return orc.Grid(deg=c.degree, nc=nc, lo=c.lo, hi=c.hi, dt=c.dt, vbc=c.vbc,
+                    kmax=c.poisson_kmax)
+
+
+def time_oracle(w, nsteps, warmup=0):
+    import oracle as orc
+
+    g = oracle_slab(w)
+    f = orc.init(g, w.kind, w.params)
+    if warmup:
+        orc.step_inplace(g, f, warmup)
+    t0 = time.perf_counter()
+    orc.step_inplace(g, f, nsteps)
+    dt = time.perf_counter() - t0
+    dofs = f.size
+    return {"value": dofs * nsteps / dt, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+            "sample": (f"{nsteps} Strang step(s) of the FP64 oracle on {g.nc[0]}x{g.nc[1]}x"
+                       f"{g.nc[2]}x{g.nc[3]} cells, degree {g.deg} ({dofs} dofs; the workload's "
+                       f"x-grid with a reduced v-grid), {dt:.1f} s"),
+            "seconds": dt, "dofs": dofs}
+
+
+def cpu_info():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            txt = fh.read()
+        for key in ("model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1803_02143_gb300 import configs
+
+    w = configs.workload(args.workload, args.precision)
+    import oracle as orc
+
+    orc.build()
+    g = oracle_slab(w)
+    f = orc.init(g, w.kind, w.params)
+    orc.step_inplace(g, f, max(0, min(args.warmup, 1)))
+    t0 = time.perf_counter()
+    orc.step_inplace(g, f, args.steps)
+    dt = time.perf_counter() - t0
+    value = f.size * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "oracle_sample": list(g.nc), "degree": g.deg},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+                         "sample": f"{args.steps} steps on {g.nc} cells, degree {g.deg} "
+                                   f"({f.size} dofs), host {cpu_info()}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def sweep_roofline(w, timing, steps_timed, pk, peak_src):
+    """Dominant kernel class of the timed region, against its roofline."""
+    cfg = w.cfg
+    n = cfg.n
+    esize = 8 if cfg.precision == "fp64" else 4
+    sweeps = {k: v for k, v in timing.items() if k in ("x1", "x2", "v1", "v2") and v[1] > 0}
+    kind = max(sweeps, key=lambda k: sweeps[k][0])
+    ms, cnt = sweeps[kind]
+    avg_s = ms / cnt / 1e3
+    algo_bytes = 2 * cfg.numel * esize          # read + write of f, matrices not counted
+    algo_flops = 2 * 2 * n * cfg.numel          # 2(l+1) FMA per dof
+    traffic = committed_traffic(f"{w.name}:{cfg.precision}:{kind}")
+    hbm = {"achieved": algo_bytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": algo_bytes / avg_s / 1e9 / pk["hbm_gbs"], "peak_source": peak_src}
+    if cfg.precision == "fp64":
+        clk = pk.get("sm_max_mhz", 2070.0)
+        peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": algo_flops / avg_s / 1e12, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": algo_flops / avg_s / 1e12 / peak_tf,
+                "traffic": traffic, "kernel": f"sweep_{kind}",
+                "peak_source": "FP64 FMA units x max SM clock (152 SMs x 2 FMA x 2 flop)",
+                "hbm": hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm["frac"], "traffic": traffic, "kernel": f"sweep_{kind}",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    roof["avg_launch_ms"] = ms / cnt
+    roof["per_kernel_ms_per_step"] = {k: v[0] / steps_timed for k, v in timing.items() if v[1]}
+    return roof
+
+
+def run_forward(w, steps, warmup, world, local, sample_clocks=True):
+    import torch
+
+    from paper_1803_02143_gb300 import Sldg
+
+    s = Sldg(w.cfg)
+    s.set_initial(w.kind, w.params)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if sample_clocks else None
+    barrier(world)
+    torch.cuda.synchronize()
+    s.timing(True)
+    n0 = s.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    timing = s.timing_read()
+    launches = s.launch_count - n0
+    s.timing(False)
+    ck = clocks.stop() if clocks else None
+    return s, ms, timing, launches, ck
+
+
+def run_e2e(s, w, steps):
+    """Through the C ABI with host buffers: upload f from pinned memory, one
+    Strang step, read W back, every step."""
+    import numpy as np
+    import torch
+
+    host = torch.empty(s.cfg.shape, dtype=s.cfg.dtype, pin_memory=True)
+    s.get_f(host)
+    s.step(1, history=True)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_f(host)
+        W = s.step(1, history=True)
+    t1 = time.perf_counter()
+    esize = 8 if s.cfg.precision == "fp64" else 4
+    return {"value": s.cfg.numel * steps / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": s.cfg.numel * esize, "d2h_bytes_per_step": 8,
+            "ms_per_step": 1e3 * (t1 - t0) / steps, "last_W": float(np.asarray(W)[0])}
+
+
+def run_adjoint_ratio():
+    """Adjoint/forward wall ratio on the adjoint workload (32^4, degree 1, 100
+    steps, checkpoint every 10): record+backward vs a plain forward."""
+    import torch
+
+    from paper_1803_02143_gb300 import Sldg, configs
+
+    w = configs.workload("adjoint_landau_32")
+    s = Sldg(w.cfg)
+    s.set_initial(w.kind, w.params)
+    s.step(2)
+    torch.cuda.synchronize()
+    s.set_initial(w.kind, w.params)
+    t0 = time.perf_counter()
+    s.step(w.steps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    s.set_initial(w.kind, w.params)
+    t0 = time.perf_counter()
+    s.record(w.steps, w.ckpt)
+    t_rec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J, _ = s.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    s.close()
+    return {"workload": w.name, "forward_s": t_fwd, "record_s": t_rec, "backward_s": t_bwd,
+            "adjoint_forward_ratio": (t_rec + t_bwd) / t_fwd, "J": J}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        from paper_1803_02143_gb300 import build as B
+
+        B.build()
+    barrier(world)
+    from paper_1803_02143_gb300 import configs
+
+    w = configs.workload(args.workload, args.precision)
+    pk, pk_src = peaks()
+    s, ms, timing, launches, clocks = run_forward(w, args.steps, args.warmup, world, local)
+    ms_max = max_over_ranks(ms, world)
+    value = w.cfg.numel * args.steps * world / (ms_max / 1e3)
+    roof = sweep_roofline(w, timing, args.steps, pk, pk_src)
+    e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
+    e2e["value"] = e2e["value"] * world
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    extras = {}
+    if not args.no_extras and rank == 0:
+        other = "fp32" if w.cfg.precision == "fp64" else "fp64"
+        w2 = configs.workload(args.workload, other)
+        s2, ms2, t2, _, _ = run_forward(w2, args.steps, args.warmup, 1, local, sample_clocks=False)
+        s2.close()
+        del s2
+        torch.cuda.empty_cache()
+        extras[other] = {"value": w2.cfg.numel * args.steps / (ms2 / 1e3), "unit": UNIT,
+                         "ms_per_step": ms2 / args.steps,
+                         "roofline": sweep_roofline(w2, t2, args.steps, pk, pk_src)}
+        extras["fp32_over_fp64_step_time"] = (
+            (ms2 / ms) if other == "fp32" else (ms / ms2))
+        extras["adjoint"] = run_adjoint_ratio()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle as orc
+
+        orc.build()
+        cpu = time_oracle(w, nsteps=2)
+        cpu["host"] = cpu_info()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w.cfg.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "cells": list(w.cfg.ncell), "degree": w.cfg.degree,
+                   "dofs": w.cfg.numel, "dt": w.cfg.dt, "initial": list(w.params),
+                   "l2": "inputs larger than L2 (f is %.1f GB)" % (
+                       w.cfg.numel * (8 if w.cfg.precision == "fp64" else 4) / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

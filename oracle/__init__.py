@@ -349,3 +349,12 @@ def backward(g: Grid, f0, nsteps: int, ckpt: int, cW=None):
     if rc != 0:
         raise MemoryError("orc_backward failed")
     return float(J[0]), grad, W[:nsteps]
+
+
+def step_inplace(g: Grid, f, nsteps: int = 1, kick: bool = True):
+    """Advance f (float64, C-contiguous, modified in place) by nsteps steps."""
+    assert f.dtype == np.float64 and f.flags["C_CONTIGUOUS"]
+    rc = _lib_handle().orc_step(g.c(), _p(f), int(nsteps), int(kick), None, None, None)
+    if rc != 0:
+        raise MemoryError("orc_step failed")
+    return f

@@ -1,0 +1,61 @@
+"""The five workloads: the paper's Landau damping and two-stream problems
+(Sec. 4, Eq. (iv-nl); Sec. 5, Eq. (iv-tsi)) at the sizes this library is
+measured on.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+from . import _native as N
+from .solver import Config
+
+LANDAU_LO = (0.0, 0.0, -6.0, -6.0)
+LANDAU_HI = (4 * math.pi, 4 * math.pi, 6.0, 6.0)
+TSI_LO = (0.0, 0.0, -9.0, -9.0)
+TSI_HI = (10 * math.pi, 10 * math.pi, 9.0, 9.0)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    cfg: Config
+    kind: int
+    params: tuple
+    steps: int
+    ckpt: int = 0  # checkpoint interval of the adjoint workloads
+
+
+def _landau(degree, nc, dt, eps, precision="fp64"):
+    return Config(degree=degree, ncell=(nc,) * 4, lo=LANDAU_LO, hi=LANDAU_HI, dt=dt,
+                  precision=precision)
+
+
+WORKLOADS = {
+    # linear Landau damping, 16^4 cells, degree 1, dt 0.1, 50 steps
+    "linear_landau_16": Workload("linear_landau_16", _landau(1, 16, 0.1, 0.01), N.SLDG_INIT_LANDAU,
+                                 (0.01, 0.5, 0.5), 50),
+    # nonlinear Landau damping, 64^4 cells, degree 2 (1.36e9 dofs), dt 0.05 to T = 20
+    "nonlinear_landau_64": Workload("nonlinear_landau_64", _landau(2, 64, 0.05, 0.5),
+                                    N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 400),
+    # two-stream instability, 64^2 x 128^2 cells, degree 2 (5.4e9 dofs), dt 0.05 to T = 40
+    "two_stream_64x128": Workload(
+        "two_stream_64x128",
+        Config(degree=2, ncell=(64, 64, 128, 128), lo=TSI_LO, hi=TSI_HI, dt=0.05),
+        N.SLDG_INIT_TWO_STREAM, (1e-3, 0.2, 3.0), 800),
+    # adjoint of nonlinear Landau damping, 32^4 cells, degree 1, dt 0.1, 100 steps, ckpt 10
+    "adjoint_landau_32": Workload("adjoint_landau_32", _landau(1, 32, 0.1, 0.5), N.SLDG_INIT_LANDAU,
+                                  (0.5, 0.5, 0.5), 100, ckpt=10),
+    # mixed precision forward+adjoint, 128^4 cells, degree 1 (4.3e9 dofs), fp32 f
+    "mixed_landau_128": Workload("mixed_landau_128", _landau(1, 128, 0.05, 0.5, "fp32"),
+                                 N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 200, ckpt=25),
+}
+
+
+def workload(name: str, precision: str | None = None) -> Workload:
+    w = WORKLOADS[name]
+    if precision is None or precision == w.cfg.precision:
+        return w
+    c = w.cfg
+    return Workload(w.name, Config(c.degree, c.ncell, c.lo, c.hi, c.dt, precision, c.vbc,
+                                   c.poisson_kmax), w.kind, w.params, w.steps, w.ckpt)

@@ -1,0 +1,840 @@
+// api.cu -- the C ABI of libsldg (include/sldg.h): context life cycle,
+// validation, the Gauss-Legendre basis and tables, the Strang step, the
+// adjoint driver with checkpointing, and per-kernel timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctx.h"
+#include "fields.cuh"
+
+using namespace sldg;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kMaxSmem = 227 * 1024;
+constexpr size_t kX1TileBudget = 48 * 1024;
+constexpr int kTimerPairs = 8192;
+
+// ---- Gauss-Legendre basis on [0,1] from the closed-form roots ---------------
+bool make_basis(int n, Basis* b) {
+  double x[kMaxNodes], w[kMaxNodes];
+  switch (n) {
+    case 1:
+      x[0] = 0.0;
+      w[0] = 2.0;
+      break;
+    case 2: {
+      const double a = 1.0 / std::sqrt(3.0);
+      x[0] = -a; x[1] = a;
+      w[0] = w[1] = 1.0;
+      break;
+    }
+    case 3: {
+      const double a = std::sqrt(0.6);
+      x[0] = -a; x[1] = 0.0; x[2] = a;
+      w[0] = w[2] = 5.0 / 9.0;
+      w[1] = 8.0 / 9.0;
+      break;
+    }
+    case 4: {
+      const double r = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+      const double a = std::sqrt(3.0 / 7.0 - r), c = std::sqrt(3.0 / 7.0 + r);
+      const double s30 = std::sqrt(30.0);
+      x[0] = -c; x[1] = -a; x[2] = a; x[3] = c;
+      w[0] = w[3] = (18.0 - s30) / 36.0;
+      w[1] = w[2] = (18.0 + s30) / 36.0;
+      break;
+    }
+    default:
+      return false;
+  }
+  b->n = n;
+  for (int i = 0; i < n; ++i) {
+    b->xi[i] = 0.5 * (1.0 + x[i]);
+    b->w[i] = 0.5 * w[i];
+  }
+  for (int j = 0; j < n; ++j) {
+    double p = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != j) p *= (b->xi[j] - b->xi[m]);
+    b->inv_den[j] = 1.0 / p;
+  }
+  for (int j = n; j < kMaxNodes; ++j) b->xi[j] = b->w[j] = b->inv_den[j] = 0.0;
+  return true;
+}
+
+// ---- allocation and error helpers ------------------------------------------
+template <typename P>
+int dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return SLDG_ERR_OOM;
+  }
+  return SLDG_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree(reinterpret_cast<void*>(p));
+  p = nullptr;
+}
+
+#define SLDG_TRY(expr)              \
+  do {                              \
+    int _rc = (expr);               \
+    if (_rc != SLDG_OK) return _rc; \
+  } while (0)
+
+#define SLDG_CU(expr)                                 \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) {                          \
+      cudaGetLastError();                             \
+      return SLDG_ERR_CUDA;                           \
+    }                                                 \
+  } while (0)
+
+// ---- per-launch timing ---------------------------------------------------------
+struct KTimer {
+  sldg_ctx* c;
+  int kind;
+  long long n;
+  size_t idx;
+  bool on;
+  KTimer(sldg_ctx* ctx, int k, long long nlaunch = 1) : c(ctx), kind(k), n(nlaunch), idx(0), on(false) {
+    if (c->timing && c->ev_used < c->ev_kind.size()) {
+      idx = c->ev_used++;
+      c->ev_kind[idx] = k;
+      cudaEventRecord(c->ev_pool[2 * idx], c->stream);
+      on = true;
+    }
+  }
+  ~KTimer() {
+    if (on) cudaEventRecord(c->ev_pool[2 * idx + 1], c->stream);
+    c->launches += n;
+    if (c->timing) c->acc_n[kind] += n;
+  }
+};
+
+// ---- grid helpers ------------------------------------------------------------------
+double node_coord(const sldg_ctx* c, int d, long long i) {
+  const int n = c->g.n;
+  return c->cfg.lo[d] + ((double)(i / n) + c->basis.xi[i % n]) * c->g.h[d];
+}
+
+double node_weight(const sldg_ctx* c, int d, long long i) {
+  return c->g.h[d] * c->basis.w[i % c->g.n];
+}
+
+int validate(const sldg_config* cfg) {
+  if (cfg->degree < 0 || cfg->degree > 3) return SLDG_ERR_BAD_CONFIG;
+  for (int d = 0; d < 4; ++d) {
+    if (cfg->ncell[d] < 2) return SLDG_ERR_BAD_CONFIG;
+    if (!(cfg->hi[d] > cfg->lo[d]) || !std::isfinite(cfg->hi[d]) || !std::isfinite(cfg->lo[d]))
+      return SLDG_ERR_BAD_CONFIG;
+  }
+  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags != 0) return SLDG_ERR_BAD_CONFIG;
+  return SLDG_OK;
+}
+
+int x1_lines_per_tile(const sldg_ctx* c) {
+  const long long D0 = c->g.D[0], D1 = c->g.D[1];
+  int best = 1;
+  for (int R = 1; R <= 64 && R <= D1; ++R) {
+    if (D1 % R) continue;
+    if (sweep_smem_bytes(c->prec, 0, D0, R) <= kX1TileBudget) best = R;
+  }
+  return best;
+}
+
+void free_all(sldg_ctx* c) {
+  for (int d = 0; d < 4; ++d) dfree(c->d_w[d]);
+  dfree(c->d_z[0]);  // coordinates are one allocation
+  for (int d = 1; d < 4; ++d) c->d_z[d] = nullptr;
+  dfree(c->d_wv);
+  dfree(c->d_wx);
+  for (int d = 0; d < 2; ++d) {
+    dfree(c->xm[d].ab); dfree(c->xm[d].dab); dfree(c->xm[d].s);
+    dfree(c->vm[d].ab); dfree(c->vm[d].dab); dfree(c->vm[d].s);
+    dfree(c->d_E[d]);
+    dfree(c->d_Eb[d]);
+  }
+  dfree(c->d_rho); dfree(c->d_part);
+  dfree(c->d_F1); dfree(c->d_F2); dfree(c->d_G1); dfree(c->d_G2);
+  dfree(c->d_T); dfree(c->d_R); dfree(c->d_U);
+  dfree(c->d_W); dfree(c->d_diag); dfree(c->d_Wrec); dfree(c->d_rhob); dfree(c->d_epart);
+  dfree(c->d_ckpool); dfree(c->d_seg);
+  for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
+  for (auto& e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+}
+
+PoissonArgs poisson_args(sldg_ctx* c) {
+  PoissonArgs a;
+  a.D0 = (int)c->g.D[0];
+  a.D1 = (int)c->g.D[1];
+  a.K0 = c->K[0];
+  a.K1 = c->K[1];
+  a.k0 = c->kap[0];
+  a.k1 = c->kap[1];
+  a.F1 = c->d_F1; a.F2 = c->d_F2; a.G1 = c->d_G1; a.G2 = c->d_G2;
+  a.T = c->d_T; a.R = c->d_R; a.U = c->d_U;
+  return a;
+}
+
+// ---- matrices -------------------------------------------------------------------
+int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv) {
+  const size_t nn = (size_t)c->g.n * c->g.n;
+  if (!m->ab) {
+    SLDG_TRY(dalloc(&m->ab, 2 * nn * count * c->esize));
+    SLDG_TRY(dalloc(&m->s, count * sizeof(int)));
+    m->count = count;
+  }
+  if (deriv && !m->dab) SLDG_TRY(dalloc(&m->dab, 2 * nn * count * c->esize));
+  return SLDG_OK;
+}
+
+// x-sweep d (0 or 1): one matrix pair per node of v_{d+1}, shift v dt frac
+int ensure_xmats(sldg_ctx* c, int d, double frac) {
+  MatSet& m = c->xm[d];
+  if (m.valid && m.frac == frac) return SLDG_OK;
+  const int vd = d + 2;
+  SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false));
+  KTimer t(c, SLDG_K_VMAT);
+  SLDG_CU(launch_build_mats(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], c->basis,
+                            m.ab, nullptr, m.s, c->stream));
+  m.frac = frac;
+  m.valid = true;
+  return SLDG_OK;
+}
+
+// v-sweep d (0 or 1 for v1, v2): one pair per x-node, shift E_d dt frac
+int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv) {
+  MatSet& m = c->vm[d];
+  if (!c->have_field) return SLDG_ERR_STATE;
+  if (m.valid && m.frac == frac && (!deriv || m.with_deriv)) return SLDG_OK;
+  SLDG_TRY(alloc_matset(c, &m, c->g.Dx, deriv));
+  KTimer t(c, SLDG_K_VMAT);
+  SLDG_CU(launch_build_mats(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], c->basis,
+                            m.ab, deriv ? m.dab : nullptr, m.s, c->stream));
+  m.frac = frac;
+  m.valid = true;
+  m.with_deriv = deriv;
+  return SLDG_OK;
+}
+
+void invalidate_vmats(sldg_ctx* c) { c->vm[0].valid = c->vm[1].valid = false; }
+
+// ---- sweeps ---------------------------------------------------------------------------
+int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const void* gfwd,
+              double* Ebar) {
+  const Grid& g = c->g;
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.f = buf;
+  a.prec = c->prec;
+  a.n = g.n;
+  a.dim = dim;
+  a.nc = g.nc[dim];
+  a.adjoint = adjoint ? 1 : 0;
+  const bool ebar = adjoint && dim >= 2 && gfwd && Ebar;
+  MatSet* m;
+  if (dim < 2) {
+    SLDG_TRY(ensure_xmats(c, dim, frac));
+    m = &c->xm[dim];
+    a.periodic = 1;
+  } else {
+    SLDG_TRY(ensure_vmats(c, dim - 2, frac, ebar));
+    m = &c->vm[dim - 2];
+    a.periodic = g.vbc == SLDG_VBC_PERIODIC;
+  }
+  a.ab = m->ab;
+  a.dab = m->dab;
+  a.s = m->s;
+  a.mcount = m->count;
+  switch (dim) {
+    case 0:
+      a.inner = 1;
+      a.outer = g.N / g.D[0];
+      a.key_div = g.D[1];
+      a.key_mod = g.D[2];
+      a.lines_per_tile = x1_lines_per_tile(c);
+      break;
+    case 1:
+      a.inner = g.D[0];
+      a.outer = g.D[2] * g.D[3];
+      a.key_div = g.D[2];
+      a.key_mod = g.D[3];
+      break;
+    case 2:
+      a.inner = g.Dx;
+      a.outer = g.D[3];
+      a.key_div = 1;
+      a.key_mod = g.Dx;
+      break;
+    default:
+      a.inner = g.Dx * g.D[2];
+      a.outer = 1;
+      a.key_div = 1;
+      a.key_mod = g.Dx;
+      break;
+  }
+  if (ebar) {
+    a.g = gfwd;
+    a.epart = c->d_epart;
+  }
+  const int kind = adjoint ? (dim < 2 ? SLDG_K_ADJ_X : SLDG_K_ADJ_V) : SLDG_K_X1 + dim;
+  {
+    KTimer t(c, kind);
+    cudaError_t e = c->prec == SLDG_FP64 ? launch_sweep_f64(a, c->stream) : launch_sweep_f32(a, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SLDG_ERR_CUDA;
+    }
+  }
+  if (ebar) {
+    // Ebar[x] += dt*frac/h_v * sum over the rows of partials at x
+    const long long rows = dim == 2 ? g.D[3] : g.D[2];
+    KTimer t(c, SLDG_K_OTHER);
+    SLDG_CU(launch_sum_rows(c->d_epart, (int)rows, g.Dx, g.dt * frac / g.h[dim], Ebar, 1,
+                            c->stream));
+  }
+  return SLDG_OK;
+}
+
+int compute_fields(sldg_ctx* c, const void* buf) {
+  int nl = 0;
+  {
+    KTimer t(c, SLDG_K_RHO, 2);
+    SLDG_CU(launch_rho(c->prec, buf, c->g, c->d_wv, c->d_part, c->rho_chunks, c->d_rho, c->stream, &nl));
+  }
+  {
+    KTimer t(c, SLDG_K_POISSON, 4);
+    nl = 0;
+    SLDG_CU(launch_poisson(poisson_args(c), c->d_rho, c->d_E[0], c->d_E[1], c->stream, &nl));
+  }
+  c->have_field = true;
+  invalidate_vmats(c);
+  return SLDG_OK;
+}
+
+// One Strang step in place on buf; W(E) of the kick field to Wslot (device) if given.
+int do_step(sldg_ctx* c, void* buf, double* Wslot) {
+  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(compute_fields(c, buf));
+  if (Wslot) {
+    KTimer t(c, SLDG_K_OTHER);
+    SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream));
+  }
+  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr));
+  return SLDG_OK;
+}
+
+int ensure_W(sldg_ctx* c, int n) {
+  if (c->W_cap >= n) return SLDG_OK;
+  dfree(c->d_W);
+  int cap = std::max(n, 64);
+  SLDG_TRY(dalloc(&c->d_W, (size_t)cap * sizeof(double)));
+  c->W_cap = cap;
+  return SLDG_OK;
+}
+
+int build_tables(sldg_ctx* c) {
+  const Grid& g = c->g;
+  // node coordinates and weights
+  std::vector<double> zall, wall[4];
+  long long off[4] = {0, g.D[0], g.D[0] + g.D[1], g.D[0] + g.D[1] + g.D[2]};
+  zall.resize(g.D[0] + g.D[1] + g.D[2] + g.D[3]);
+  for (int d = 0; d < 4; ++d) {
+    wall[d].resize(g.D[d]);
+    for (long long i = 0; i < g.D[d]; ++i) {
+      zall[off[d] + i] = node_coord(c, d, i);
+      wall[d][i] = node_weight(c, d, i);
+    }
+  }
+  SLDG_TRY(dalloc(&c->d_z[0], zall.size() * sizeof(double)));
+  for (int d = 1; d < 4; ++d) c->d_z[d] = c->d_z[0] + off[d];
+  SLDG_CU(cudaMemcpy(c->d_z[0], zall.data(), zall.size() * sizeof(double), cudaMemcpyHostToDevice));
+  for (int d = 0; d < 4; ++d) {
+    SLDG_TRY(dalloc(&c->d_w[d], g.D[d] * sizeof(double)));
+    SLDG_CU(cudaMemcpy(c->d_w[d], wall[d].data(), g.D[d] * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  std::vector<double> wv(g.Dv), wx(g.Dx);
+  for (long long i3 = 0; i3 < g.D[3]; ++i3)
+    for (long long i2 = 0; i2 < g.D[2]; ++i2) wv[i3 * g.D[2] + i2] = wall[2][i2] * wall[3][i3];
+  for (long long i1 = 0; i1 < g.D[1]; ++i1)
+    for (long long i0 = 0; i0 < g.D[0]; ++i0) wx[i1 * g.D[0] + i0] = wall[0][i0] * wall[1][i1];
+  SLDG_TRY(dalloc(&c->d_wv, g.Dv * sizeof(double)));
+  SLDG_TRY(dalloc(&c->d_wx, g.Dx * sizeof(double)));
+  SLDG_CU(cudaMemcpy(c->d_wv, wv.data(), g.Dv * sizeof(double), cudaMemcpyHostToDevice));
+  SLDG_CU(cudaMemcpy(c->d_wx, wx.data(), g.Dx * sizeof(double), cudaMemcpyHostToDevice));
+
+  // spectral tables
+  for (int d = 0; d < 2; ++d) {
+    const int nc = c->cfg.ncell[d];
+    int K = (int)((g.D[d] - 1) / 2);
+    if (K > nc - 1) K = nc - 1;
+    if (c->cfg.poisson_kmax >= 0) K = c->cfg.poisson_kmax;
+    c->K[d] = K;
+    c->kap[d] = 2.0 * kPi / (c->cfg.hi[d] - c->cfg.lo[d]);
+  }
+  const int D0 = (int)g.D[0], D1 = (int)g.D[1];
+  const int M1 = c->K[0] + 1, M2 = 2 * c->K[1] + 1;
+  const double L0 = c->cfg.hi[0] - c->cfg.lo[0], L1 = c->cfg.hi[1] - c->cfg.lo[1];
+  std::vector<double2> F1((size_t)D0 * M1), G1((size_t)M1 * D0), F2((size_t)M2 * D1), G2((size_t)D1 * M2);
+  for (int n1 = 0; n1 < D0; ++n1)
+    for (int m1 = 0; m1 < M1; ++m1) {
+      const double ph = c->kap[0] * m1 * zall[off[0] + n1];
+      const double wl = wall[0][n1] / L0;
+      F1[(size_t)n1 * M1 + m1] = make_double2(wl * std::cos(ph), -wl * std::sin(ph));
+      G1[(size_t)m1 * D0 + n1] = make_double2(std::cos(ph), std::sin(ph));
+    }
+  for (int mi = 0; mi < M2; ++mi)
+    for (int n2 = 0; n2 < D1; ++n2) {
+      const double ph = c->kap[1] * (mi - c->K[1]) * zall[off[1] + n2];
+      const double wl = wall[1][n2] / L1;
+      F2[(size_t)mi * D1 + n2] = make_double2(wl * std::cos(ph), -wl * std::sin(ph));
+      G2[(size_t)n2 * M2 + mi] = make_double2(std::cos(ph), std::sin(ph));
+    }
+  SLDG_TRY(dalloc(&c->d_F1, F1.size() * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_G1, G1.size() * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_F2, F2.size() * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_G2, G2.size() * sizeof(double2)));
+  SLDG_CU(cudaMemcpy(c->d_F1, F1.data(), F1.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  SLDG_CU(cudaMemcpy(c->d_G1, G1.data(), G1.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  SLDG_CU(cudaMemcpy(c->d_F2, F2.data(), F2.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  SLDG_CU(cudaMemcpy(c->d_G2, G2.data(), G2.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  SLDG_TRY(dalloc(&c->d_T, (size_t)D1 * M1 * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_R, (size_t)M2 * M1 * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_U, 2 * (size_t)D1 * M1 * sizeof(double2)));
+  return SLDG_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+const char* sldg_strerror(int code) {
+  switch (code) {
+    case SLDG_OK: return "ok";
+    case SLDG_ERR_BAD_CONFIG: return "invalid or unsupported configuration";
+    case SLDG_ERR_BAD_PTR: return "null or misaligned pointer";
+    case SLDG_ERR_OOM: return "out of memory";
+    case SLDG_ERR_CUDA: return "CUDA runtime error";
+    case SLDG_ERR_NONFINITE: return "non-finite value in f";
+    case SLDG_ERR_UNSUPPORTED: return "size not supported by the kernels";
+    case SLDG_ERR_STATE: return "call out of order";
+    case SLDG_ERR_ARG: return "invalid argument";
+    default: return "unknown status";
+  }
+}
+
+int sldg_abi_version(void) { return 1; }
+
+int sldg_init(const sldg_config* cfg, void* f_dev, void* stream, sldg_ctx** out) {
+  if (!cfg || !out) return SLDG_ERR_BAD_PTR;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != SLDG_OK) return rc;
+  if (!f_dev || (reinterpret_cast<uintptr_t>(f_dev) & 15)) return SLDG_ERR_BAD_PTR;
+  sldg_ctx* c = new (std::nothrow) sldg_ctx();
+  if (!c) return SLDG_ERR_OOM;
+  c->cfg = *cfg;
+  c->prec = cfg->precision;
+  c->esize = cfg->precision == SLDG_FP64 ? sizeof(double) : sizeof(float);
+  c->f = f_dev;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  make_basis(cfg->degree + 1, &c->basis);
+  Grid& g = c->g;
+  g.n = cfg->degree + 1;
+  for (int d = 0; d < 4; ++d) {
+    g.nc[d] = cfg->ncell[d];
+    g.D[d] = (long long)cfg->ncell[d] * g.n;
+    g.lo[d] = cfg->lo[d];
+    g.h[d] = (cfg->hi[d] - cfg->lo[d]) / cfg->ncell[d];
+  }
+  g.dt = cfg->dt;
+  g.vbc = cfg->vbc;
+  g.Dx = g.D[0] * g.D[1];
+  g.Dv = g.D[2] * g.D[3];
+  g.N = g.Dx * g.Dv;
+  // on-chip staging limits: a whole line (x1) or a 32-column tile (x2, v1, v2)
+  if (sweep_smem_bytes(c->prec, 0, g.D[0], 1) > kMaxSmem) rc = SLDG_ERR_BAD_CONFIG;
+  for (int d = 1; d < 4; ++d)
+    if (sweep_smem_bytes(c->prec, d, g.D[d], 1) > kMaxSmem) rc = SLDG_ERR_BAD_CONFIG;
+  if (g.D[0] > 2048 || g.D[1] > 65535 || g.Dx > (1LL << 31)) rc = SLDG_ERR_BAD_CONFIG;
+  for (int d = 0; d < 2; ++d)  // modes beyond (D-1)/2 are not resolved by D nodes
+    if (cfg->poisson_kmax > (g.D[d] - 1) / 2) rc = SLDG_ERR_BAD_CONFIG;
+  if (rc == SLDG_OK) rc = build_tables(c);
+  if (rc == SLDG_OK) {
+    for (int d = 0; d < 2; ++d) rc = rc ? rc : dalloc(&c->d_E[d], g.Dx * sizeof(double));
+  }
+  if (rc == SLDG_OK) rc = dalloc(&c->d_rho, g.Dx * sizeof(double));
+  if (rc == SLDG_OK) {
+    // rho partial rows: enough blocks to fill the GPU, at least 64 v-planes each
+    long long ch = std::max<long long>(1, std::min<long long>(32, g.Dv / 64));
+    c->rho_chunks = (int)ch;
+    const size_t tabn = (size_t)(g.D[0] + g.D[1] + g.D[2] + g.D[3]);
+    c->part_elems = std::max<size_t>((size_t)ch * g.Dx, diag_scratch_doubles() + tabn + 2);
+    rc = dalloc(&c->d_part, c->part_elems * sizeof(double));
+  }
+  if (rc == SLDG_OK) rc = dalloc(&c->d_diag, 16 * sizeof(double));
+  if (rc == SLDG_OK) rc = ensure_W(c, 64);
+  if (rc == SLDG_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = SLDG_ERR_CUDA;
+  }
+  if (rc != SLDG_OK) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return SLDG_OK;
+}
+
+void sldg_destroy(sldg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+long long sldg_numel(const sldg_ctx* c) { return c ? c->g.N : 0; }
+
+int sldg_bind(sldg_ctx* c, void* f_dev) {
+  if (!c || !f_dev || (reinterpret_cast<uintptr_t>(f_dev) & 15)) return SLDG_ERR_BAD_PTR;
+  c->f = f_dev;
+  return SLDG_OK;
+}
+
+int sldg_set_initial(sldg_ctx* c, int kind, const double* params, int nparams) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (!params) return SLDG_ERR_BAD_PTR;
+  if (kind < 0 || kind > 2 || nparams < 3) return SLDG_ERR_ARG;
+  double* tab = c->d_part;  // D0+D1+D2+D3 doubles of scratch
+  if (c->part_elems < (size_t)(c->g.D[0] + c->g.D[1] + c->g.D[2] + c->g.D[3])) return SLDG_ERR_UNSUPPORTED;
+  int nl = 0;
+  KTimer t(c, SLDG_K_OTHER, 2);
+  SLDG_CU(launch_init(c->prec, c->f, c->g, kind, params, c->d_z[0], tab, c->stream, &nl));
+  c->t = 0.0;
+  c->step = 0;
+  c->have_field = false;
+  invalidate_vmats(c);
+  return SLDG_OK;
+}
+
+int sldg_get_f(sldg_ctx* c, void* dst, int on_device) {
+  if (!c || !dst) return SLDG_ERR_BAD_PTR;
+  SLDG_CU(cudaMemcpyAsync(dst, c->f, c->g.N * c->esize,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!on_device) SLDG_CU(cudaStreamSynchronize(c->stream));
+  return SLDG_OK;
+}
+
+int sldg_set_f(sldg_ctx* c, const void* src, int on_device, double t, long long step) {
+  if (!c || !src) return SLDG_ERR_BAD_PTR;
+  SLDG_CU(cudaMemcpyAsync(c->f, src, c->g.N * c->esize,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  c->t = t;
+  c->step = step;
+  c->have_field = false;
+  invalidate_vmats(c);
+  return SLDG_OK;
+}
+
+int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (nsteps < 0) return SLDG_ERR_ARG;
+  if (W_history) SLDG_TRY(ensure_W(c, nsteps));
+  for (int m = 0; m < nsteps; ++m) {
+    SLDG_TRY(do_step(c, c->f, W_history ? c->d_W + m : nullptr));
+    c->t += c->g.dt;
+    c->step += 1;
+  }
+  if (W_history && nsteps > 0) {
+    SLDG_CU(cudaMemcpyAsync(W_history, c->d_W, nsteps * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    SLDG_CU(cudaStreamSynchronize(c->stream));
+  }
+  return SLDG_OK;
+}
+
+int sldg_sweep(sldg_ctx* c, int dim, double frac) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (dim < 0 || dim > 3 || !std::isfinite(frac)) return SLDG_ERR_ARG;
+  return run_sweep(c, c->f, dim, frac, false, nullptr, nullptr);
+}
+
+int sldg_compute_fields(sldg_ctx* c) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  return compute_fields(c, c->f);
+}
+
+int sldg_set_field(sldg_ctx* c, const double* E1, const double* E2, int on_device) {
+  if (!c || !E1 || !E2) return SLDG_ERR_BAD_PTR;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SLDG_CU(cudaMemcpyAsync(c->d_E[0], E1, c->g.Dx * sizeof(double), k, c->stream));
+  SLDG_CU(cudaMemcpyAsync(c->d_E[1], E2, c->g.Dx * sizeof(double), k, c->stream));
+  if (!on_device) SLDG_CU(cudaStreamSynchronize(c->stream));
+  c->have_field = true;
+  invalidate_vmats(c);
+  return SLDG_OK;
+}
+
+int sldg_fields(sldg_ctx* c, double* rho, double* E1, double* E2, int on_device) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t b = c->g.Dx * sizeof(double);
+  if (rho) SLDG_CU(cudaMemcpyAsync(rho, c->d_rho, b, k, c->stream));
+  if (E1) SLDG_CU(cudaMemcpyAsync(E1, c->d_E[0], b, k, c->stream));
+  if (E2) SLDG_CU(cudaMemcpyAsync(E2, c->d_E[1], b, k, c->stream));
+  if (!on_device) SLDG_CU(cudaStreamSynchronize(c->stream));
+  return SLDG_OK;
+}
+
+int sldg_diagnostics(sldg_ctx* c, sldg_diag* out) {
+  if (!c || !out) return SLDG_ERR_BAD_PTR;
+  SLDG_TRY(compute_fields(c, c->f));
+  int nl = 0;
+  {
+    KTimer t(c, SLDG_K_OTHER, 3);
+    SLDG_CU(launch_diag(c->prec, c->f, c->g, c->d_wx, c->d_wv, c->d_z[2], c->d_z[3], c->d_part,
+                        c->d_diag, c->stream, &nl));
+    SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, c->d_diag + 4, c->stream));
+  }
+  double h[5];
+  SLDG_CU(cudaMemcpyAsync(h, c->d_diag, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  out->t = c->t;
+  out->step = c->step;
+  out->mass = h[0];
+  out->l1 = h[1];
+  out->l2sq = h[2];
+  out->kinetic = h[3];
+  out->electric = h[4];
+  out->total = h[3] + h[4];
+  for (int i = 0; i < 5; ++i)
+    if (!std::isfinite(h[i])) return SLDG_ERR_NONFINITE;
+  return SLDG_OK;
+}
+
+// ---- adjoint ------------------------------------------------------------------------
+static int ensure_adjoint_scratch(sldg_ctx* c) {
+  const Grid& g = c->g;
+  for (int d = 0; d < 2; ++d)
+    if (!c->d_Eb[d]) SLDG_TRY(dalloc(&c->d_Eb[d], g.Dx * sizeof(double)));
+  if (!c->d_rhob) SLDG_TRY(dalloc(&c->d_rhob, g.Dx * sizeof(double)));
+  const size_t need = (size_t)std::max(g.D[2], g.D[3]) * g.Dx;
+  if (c->epart_elems < need) {
+    dfree(c->d_epart);
+    SLDG_TRY(dalloc(&c->d_epart, need * sizeof(double)));
+    c->epart_elems = need;
+  }
+  return SLDG_OK;
+}
+
+int sldg_sweep_adjoint(sldg_ctx* c, int dim, double frac, void* lam, const void* g, double* Ebar) {
+  if (!c || !lam) return SLDG_ERR_BAD_PTR;
+  if (dim < 0 || dim > 3 || !std::isfinite(frac)) return SLDG_ERR_ARG;
+  if ((g == nullptr) != (Ebar == nullptr)) return SLDG_ERR_ARG;
+  if (g && dim < 2) return SLDG_ERR_ARG;
+  if (g) SLDG_TRY(ensure_adjoint_scratch(c));
+  return run_sweep(c, lam, dim, frac, true, g, Ebar);
+}
+
+int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (nsteps < 1 || ckpt_every < 1) return SLDG_ERR_ARG;
+  const size_t fb = c->g.N * c->esize;
+  const size_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
+  const size_t seg = std::min(ckpt_every, nsteps);
+  dfree(c->d_ckpool);
+  dfree(c->d_seg);
+  for (int i = 0; i < 2; ++i) dfree(c->d_work[i]);
+  dfree(c->d_Wrec);
+  c->recorded = false;
+  SLDG_TRY(dalloc(&c->d_ckpool, nck * fb));
+  SLDG_TRY(dalloc(&c->d_seg, seg * fb));
+  SLDG_TRY(dalloc(&c->d_work[0], fb));
+  SLDG_TRY(dalloc(&c->d_work[1], fb));
+  SLDG_TRY(dalloc(&c->d_Wrec, nsteps * sizeof(double)));
+  SLDG_TRY(ensure_adjoint_scratch(c));
+  c->ck_count = nck;
+  c->seg_count = seg;
+  c->rec_t0 = c->t;
+  c->rec_step0 = c->step;
+  for (int m = 0; m < nsteps; ++m) {
+    if (m % ckpt_every == 0) {
+      char* dst = reinterpret_cast<char*>(c->d_ckpool) + (size_t)(m / ckpt_every) * fb;
+      SLDG_CU(cudaMemcpyAsync(dst, c->f, fb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    SLDG_TRY(do_step(c, c->f, c->d_Wrec + m));
+    c->t += c->g.dt;
+    c->step += 1;
+  }
+  if (W_history) {
+    SLDG_CU(cudaMemcpyAsync(W_history, c->d_Wrec, nsteps * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    SLDG_CU(cudaStreamSynchronize(c->stream));
+  }
+  c->rec_nsteps = nsteps;
+  c->rec_ckpt = ckpt_every;
+  c->recorded = true;
+  return SLDG_OK;
+}
+
+int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
+  if (!c || !grad) return SLDG_ERR_BAD_PTR;
+  if (!c->recorded) return SLDG_ERR_STATE;
+  const Grid& g = c->g;
+  const int n = c->rec_nsteps, ck = c->rec_ckpt;
+  const size_t fb = g.N * c->esize;
+  char* pool = reinterpret_cast<char*>(c->d_ckpool);
+  char* seg = reinterpret_cast<char*>(c->d_seg);
+  void* g2 = c->d_work[0];
+  void* g3 = c->d_work[1];
+  // J from the recorded W history (compensated host sum)
+  if (J_out) {
+    std::vector<double> W(n);
+    SLDG_CU(cudaMemcpyAsync(W.data(), c->d_Wrec, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SLDG_CU(cudaStreamSynchronize(c->stream));
+    double s = 0.0, comp = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const double x = (cW ? cW[m] : g.dt) * W[m];
+      const double t = s + x;
+      comp += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    *J_out = s + comp;
+  }
+  SLDG_CU(cudaMemsetAsync(grad, 0, fb, c->stream));
+  const int nseg = (int)c->ck_count;
+  for (int sidx = nseg - 1; sidx >= 0; --sidx) {
+    const int m0 = sidx * ck, m1 = std::min(m0 + ck, n);
+    SLDG_CU(cudaMemcpyAsync(seg, pool + (size_t)sidx * fb, fb, cudaMemcpyDeviceToDevice, c->stream));
+    for (int m = m0; m < m1 - 1; ++m) {
+      char* cur = seg + (size_t)(m - m0) * fb;
+      SLDG_CU(cudaMemcpyAsync(cur + fb, cur, fb, cudaMemcpyDeviceToDevice, c->stream));
+      SLDG_TRY(do_step(c, cur + fb, nullptr));
+    }
+    for (int m = m1 - 1; m >= m0; --m) {
+      const char* fm = seg + (size_t)(m - m0) * fb;
+      // forward intermediates: g2 = X2 X1 f^m (input of V1), g3 = V1 g2 (input of V2)
+      SLDG_CU(cudaMemcpyAsync(g2, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
+      SLDG_TRY(run_sweep(c, g2, 0, 0.5, false, nullptr, nullptr));
+      SLDG_TRY(run_sweep(c, g2, 1, 0.5, false, nullptr, nullptr));
+      SLDG_TRY(compute_fields(c, g2));
+      SLDG_CU(cudaMemcpyAsync(g3, g2, fb, cudaMemcpyDeviceToDevice, c->stream));
+      SLDG_TRY(run_sweep(c, g3, 2, 1.0, false, nullptr, nullptr));
+      // reverse
+      SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
+      SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
+      SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
+      SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
+      SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1]));
+      SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0]));
+      {
+        KTimer t(c, SLDG_K_OTHER);
+        SLDG_CU(launch_energy_adj(c->d_Eb[0], c->d_Eb[1], c->d_E[0], c->d_E[1], c->d_wx, g.Dx,
+                                  cW ? cW[m] : g.dt, c->stream));
+      }
+      {
+        int nl = 0;
+        KTimer t(c, SLDG_K_POISSON, 4);
+        SLDG_CU(launch_poisson_adj(poisson_args(c), c->d_Eb[0], c->d_Eb[1], c->d_rhob, c->stream, &nl));
+      }
+      {
+        KTimer t(c, SLDG_K_RHO);
+        SLDG_CU(launch_rho_adj(c->prec, grad, g, c->d_wv, c->d_rhob, c->stream));
+      }
+      SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
+      SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
+    }
+  }
+  // the context's field now belongs to the first step; leave f as recorded
+  c->have_field = false;
+  invalidate_vmats(c);
+  return SLDG_OK;
+}
+
+int sldg_initial_param_grad(sldg_ctx* c, int kind, const double* params, int nparams,
+                            const void* grad, double* out) {
+  if (!c || !params || !grad || !out) return SLDG_ERR_BAD_PTR;
+  if (kind < 0 || kind > 2 || nparams < 3) return SLDG_ERR_ARG;
+  const Grid& g = c->g;
+  const size_t tabn = g.D[0] + g.D[1] + g.D[2] + g.D[3];
+  if (c->part_elems < tabn + diag_scratch_doubles() + 2) {
+    // scratch layout: [tab][partials][result]
+    dfree(c->d_part);
+    c->part_elems = std::max(c->part_elems, tabn + diag_scratch_doubles() + 2);
+    SLDG_TRY(dalloc(&c->d_part, c->part_elems * sizeof(double)));
+  }
+  double* tab = c->d_part;
+  double* scratch = c->d_part + tabn;
+  double* res = c->d_part + tabn + diag_scratch_doubles();
+  int nl = 0;
+  {
+    KTimer t(c, SLDG_K_OTHER, 3);
+    SLDG_CU(launch_param_grad(c->prec, grad, g, kind, params, c->d_z[0], tab, scratch, res, c->stream, &nl));
+  }
+  SLDG_CU(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  return SLDG_OK;
+}
+
+// ---- measurement ----------------------------------------------------------------------
+long long sldg_launch_count(const sldg_ctx* c) { return c ? c->launches : 0; }
+
+int sldg_timing(sldg_ctx* c, int enable) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  if (enable && c->ev_pool.empty()) {
+    c->ev_pool.resize(2 * kTimerPairs);
+    for (auto& e : c->ev_pool) SLDG_CU(cudaEventCreate(&e));
+    c->ev_kind.assign(kTimerPairs, 0);
+  }
+  c->timing = enable != 0;
+  c->ev_used = 0;
+  for (int k = 0; k < SLDG_NUM_KINDS; ++k) {
+    c->acc_ms[k] = 0.0;
+    c->acc_n[k] = 0;
+  }
+  return SLDG_OK;
+}
+
+int sldg_timing_read(sldg_ctx* c, double* ms, long long* count) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    float t = 0.f;
+    SLDG_CU(cudaEventElapsedTime(&t, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
+    c->acc_ms[c->ev_kind[i]] += t;
+  }
+  c->ev_used = 0;
+  for (int k = 0; k < SLDG_NUM_KINDS; ++k) {
+    if (ms) ms[k] = c->acc_ms[k];
+    if (count) count[k] = c->acc_n[k];
+  }
+  return SLDG_OK;
+}
+
+}  // extern "C"

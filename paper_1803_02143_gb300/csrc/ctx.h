@@ -1,0 +1,130 @@
+// ctx.h -- host-side context of libsldg and the launch interface between
+// its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace sldg {
+
+// Matrices of one family of shifts, structure-of-arrays so that consecutive
+// threads (consecutive keys) read consecutive addresses:
+//   ab[(k * count) + key], k = 0..n*n-1 for A (row-major), n*n..2n*n-1 for B;
+//   dab likewise for dA/dtheta, dB/dtheta (only when derivatives requested);
+//   s[key] the integer cell shift.
+struct MatSet {
+  void* ab = nullptr;   // element type of the context precision
+  void* dab = nullptr;  // same precision, derivative matrices
+  int* s = nullptr;
+  long long count = 0;
+  double frac = 0.0;    // shift scale these matrices were built for
+  bool valid = false;
+  bool with_deriv = false;
+};
+
+// Everything a sweep launch needs.
+struct SweepArgs {
+  void* f;             // in place, N elements
+  const void* g;       // forward input for the shift derivative (adjoint v-sweeps), or null
+  double* epart;       // partial sums of the shift derivative, or null
+  int prec;            // SLDG_FP64 / SLDG_FP32
+  int n;               // nodes per cell
+  int dim;             // 0..3
+  int nc;              // cells along dim
+  long long inner;     // elements between consecutive nodes along dim
+  long long outer;     // number of (D x inner) blocks
+  const void* ab;      // matrices (SoA), see MatSet
+  const void* dab;
+  const int* s;
+  long long mcount;    // keys in the matrix set
+  long long key_div;   // x-sweeps: key = (line or block index / key_div) % key_mod
+  long long key_mod;   // v-sweeps: key = column % key_mod
+  int periodic;
+  int adjoint;
+  int lines_per_tile;  // x1-sweep tile height R (divides D1)
+};
+
+// Kernel launchers (sweep_f64.cu / sweep_f32.cu).
+cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
+size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
+
+}  // namespace sldg
+
+struct sldg_ctx {
+  sldg_config cfg;
+  sldg::Grid g;
+  sldg::Basis basis;
+  int prec;
+  size_t esize;
+  void* f;
+  cudaStream_t stream;
+
+  // per-direction node coordinates and weights (device, D_d doubles)
+  double* d_z[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d_w[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d_wv = nullptr;  // v-plane weights w_v1 * w_v2, Dv doubles
+  double* d_wx = nullptr;  // x-plane weights w_x1 * w_x2, Dx doubles
+
+  sldg::MatSet xm[2];  // x1: key v1 node, x2: key v2 node
+  sldg::MatSet vm[2];  // v1, v2: key x-node
+
+  // fields
+  double* d_rho = nullptr;
+  double* d_E[2] = {nullptr, nullptr};
+  bool have_field = false;
+
+  // reduction scratch
+  double* d_part = nullptr;
+  size_t part_elems = 0;
+  int rho_chunks = 1;
+
+  // spectral tables (complex as double2), K = modes per direction
+  int K[2] = {0, 0};
+  double2* d_F1 = nullptr;  // [D0][K0+1]   w_n/L exp(-i k m z_n), m >= 0
+  double2* d_F2 = nullptr;  // [2K1+1][D1]  w_n/L exp(-i k m z_n), m = -K1..K1
+  double2* d_G1 = nullptr;  // [K0+1][D0]   exp(+i k m z_n)
+  double2* d_G2 = nullptr;  // [D1][2K1+1]  exp(+i k m z_n)
+  double2* d_T = nullptr;   // work [D1][K0+1]
+  double2* d_R = nullptr;   // work [2K1+1][K0+1]
+  double2* d_U = nullptr;   // work 2 x [D1][K0+1]
+  double kap[2] = {0.0, 0.0};
+
+  // per-step electric energy (device) and diagnostics scratch
+  double* d_W = nullptr;
+  int W_cap = 0;
+  double* d_diag = nullptr;  // small result buffer
+
+  // adjoint
+  void* d_ckpool = nullptr;  // checkpoints
+  size_t ck_count = 0;
+  int rec_nsteps = 0, rec_ckpt = 0;
+  bool recorded = false;
+  double* d_Wrec = nullptr;
+  void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};  // g2, g3, lam, seg...
+  void* d_seg = nullptr;
+  size_t seg_count = 0;
+  double* d_Eb[2] = {nullptr, nullptr};
+  double* d_rhob = nullptr;
+  double* d_epart = nullptr;
+  size_t epart_elems = 0;
+  void* rec_f0_state = nullptr;
+  double rec_t0 = 0.0;
+  long long rec_step0 = 0;
+
+  // state
+  double t = 0.0;
+  long long step = 0;
+  long long launches = 0;
+
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kind per recorded pair
+  size_t ev_used = 0;        // pairs used
+  double acc_ms[SLDG_NUM_KINDS] = {0};
+  long long acc_n[SLDG_NUM_KINDS] = {0};
+};

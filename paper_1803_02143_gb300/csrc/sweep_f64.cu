@@ -1,0 +1,15 @@
+// sweep_f64.cu -- FP64 instantiations of the sweep kernels.
+#include "sweep_kernels.cuh"
+
+namespace sldg {
+
+cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st) {
+  return launch_sweep_any<double>(a, st);
+}
+
+size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile) {
+  const size_t es = prec == SLDG_FP64 ? sizeof(double) : sizeof(float);
+  return dim == 0 ? x1_smem(es, D, lines_per_tile) : strided_smem(es, D);
+}
+
+}  // namespace sldg

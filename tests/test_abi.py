@@ -1,0 +1,96 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/sldg.h declares; host-side validation answers without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_02143_gb300 import build
+
+    build.build()
+    from paper_1803_02143_gb300 import _native
+
+    return _native.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sldg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sldg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("sldg_init", "sldg_step", "sldg_fields", "sldg_diagnostics", "sldg_backward",
+                 "sldg_sweep", "sldg_sweep_adjoint", "sldg_record"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1803_02143_gb300 import _native
+
+    assert sorted(_native.SIGNATURES) == _declared()
+
+
+def test_strerror_names_every_code(lib):
+    from paper_1803_02143_gb300 import _native as N
+
+    for code in range(0, -9, -1):
+        s = N.sldg_strerror(code)
+        assert s and s != "unknown status"
+    assert N.sldg_strerror(-99) == "unknown status"
+    assert N.sldg_abi_version() == 1
+
+
+def _cfg(**kw):
+    from paper_1803_02143_gb300 import Config
+
+    base = dict(degree=1, ncell=(4, 4, 4, 4), lo=(0, 0, -6, -6), hi=(12.56, 12.56, 6, 6), dt=0.1)
+    base.update(kw)
+    return Config(**base).c()
+
+
+@pytest.mark.parametrize("bad", [dict(degree=4), dict(degree=-1), dict(ncell=(1, 4, 4, 4)),
+                                 dict(dt=0.0), dict(dt=float("nan")),
+                                 dict(hi=(0.0, 12.56, 6, 6))])
+def test_init_rejects_invalid_config_on_host(lib, bad):
+    # validation happens before any CUDA call
+    from paper_1803_02143_gb300 import _native as N
+
+    out = ctypes.c_void_p()
+    rc = lib.sldg_init(ctypes.byref(_cfg(**bad)), ctypes.c_void_p(16), None, ctypes.byref(out))
+    assert rc == N.SLDG_ERR_BAD_CONFIG and not out.value
+
+
+def test_init_rejects_bad_pointers_on_host(lib):
+    from paper_1803_02143_gb300 import _native as N
+
+    out = ctypes.c_void_p()
+    assert lib.sldg_init(None, ctypes.c_void_p(16), None, ctypes.byref(out)) == N.SLDG_ERR_BAD_PTR
+    c = _cfg()
+    assert lib.sldg_init(ctypes.byref(c), None, None, ctypes.byref(out)) == N.SLDG_ERR_BAD_PTR
+    assert lib.sldg_init(ctypes.byref(c), ctypes.c_void_p(24), None,
+                         ctypes.byref(out)) == N.SLDG_ERR_BAD_PTR  # misaligned
+    c.flags = 1
+    assert lib.sldg_init(ctypes.byref(c), ctypes.c_void_p(16), None,
+                         ctypes.byref(out)) == N.SLDG_ERR_BAD_CONFIG
+
+
+def test_null_context_is_rejected(lib):
+    from paper_1803_02143_gb300 import _native as N
+
+    assert lib.sldg_step(None, 1, None) == N.SLDG_ERR_BAD_PTR
+    assert lib.sldg_sweep(None, 0, 0.5) == N.SLDG_ERR_BAD_PTR
+    assert lib.sldg_numel(None) == 0
+    lib.sldg_destroy(None)

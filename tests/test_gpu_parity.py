@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Grids are chosen so that tiles are ragged (line lengths and column counts
+that are not multiples of the 32-wide tiles) and several tiles are spanned;
+v-shifts cover several cells.  Tolerances: FP64 per operation 1e-13 and
+per Strang step 1e-12 relative to max|f| (the per-step bound of the
+specification); FP32 storage within the rounding of single precision.
+"""
+import numpy as np
+import pytest
+
+from inputs import LANDAU_HI, LANDAU_LO, TSI_HI, TSI_LO, random_f, random_field, smooth_field
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-13     # one sweep / reduction, relative to max|.|
+TOL64_STEP = 1e-12
+TOL32 = 3e-6      # one FP32 sweep against the FP64 oracle on the same (rounded) input
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_02143_gb300 import build
+
+    build.build()
+    import paper_1803_02143_gb300 as P
+
+    return P
+
+
+def make(P, orc, deg, nc, lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1, prec="fp64", vbc=0, kmax=-1):
+    cfg = P.Config(degree=deg, ncell=nc, lo=lo, hi=hi, dt=dt, precision=prec, vbc=vbc,
+                   poisson_kmax=kmax)
+    og = orc.Grid(deg=deg, nc=nc, lo=lo, hi=hi, dt=dt, vbc=vbc, kmax=kmax)
+    return P.Sldg(cfg), og
+
+
+def put(s, arr):
+    s.f.copy_(torch.from_numpy(np.ascontiguousarray(arr).reshape(s.cfg.shape)).to(s.cfg.dtype))
+
+
+def get(s):
+    torch.cuda.synchronize()
+    return s.f.double().cpu().numpy().reshape(s.cfg.shape)
+
+
+def relerr(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+GRIDS = [
+    (1, (5, 3, 7, 6)),     # every dimension ragged and short
+    (2, (13, 11, 12, 9)),  # D = 39, 33, 36, 27: several tiles, ragged tails
+    (3, (4, 6, 5, 7)),
+    (0, (9, 8, 10, 7)),
+]
+
+
+@pytest.mark.parametrize("deg,nc", GRIDS)
+@pytest.mark.parametrize("dim", [0, 1, 2, 3])
+@pytest.mark.parametrize("vbc", [0, 1])
+def test_sweep_fp64(lib, orc, deg, nc, dim, vbc):
+    s, og = make(lib, orc, deg, nc, vbc=vbc, dt=0.37)
+    f = random_f(og.shape, seed=100 + dim)
+    put(s, f)
+    frac = 0.5 if dim < 2 else 1.0
+    E = None
+    if dim >= 2:
+        # fields up to ~3 cells of shift, both signs
+        E1 = random_field(og.xshape, seed=7, scale=2.5 * og.h(2) / og.dt)
+        E2 = random_field(og.xshape, seed=8, scale=2.5 * og.h(3) / og.dt)
+        s.set_field(torch.from_numpy(E1), torch.from_numpy(E2))
+        E = E1 if dim == 2 else E2
+    s.sweep(dim, frac)
+    ref = orc.sweep(og, dim, f, Ed=E, frac=frac).reshape(og.shape)
+    assert relerr(get(s), ref) < TOL64
+    s.close()
+
+
+@pytest.mark.parametrize("deg,nc", GRIDS[:2])
+@pytest.mark.parametrize("dim", [0, 1, 2, 3])
+def test_sweep_fp32(lib, orc, deg, nc, dim):
+    s, og = make(lib, orc, deg, nc, dt=0.37, prec="fp32")
+    f = random_f(og.shape, seed=200 + dim).astype(np.float32).astype(np.float64)
+    put(s, f)
+    frac = 0.5 if dim < 2 else 1.0
+    E = None
+    if dim >= 2:
+        E1 = random_field(og.xshape, seed=9, scale=1.5 * og.h(2) / og.dt)
+        E2 = random_field(og.xshape, seed=10, scale=1.5 * og.h(3) / og.dt)
+        s.set_field(torch.from_numpy(E1), torch.from_numpy(E2))
+        E = E1 if dim == 2 else E2
+    s.sweep(dim, frac)
+    ref = orc.sweep(og, dim, f, Ed=E, frac=frac).reshape(og.shape)
+    assert relerr(get(s), ref) < TOL32
+    s.close()
+
+
+@pytest.mark.parametrize("deg,nc", GRIDS[:3])
+@pytest.mark.parametrize("dim", [0, 1, 2, 3])
+@pytest.mark.parametrize("vbc", [0, 1])
+def test_sweep_adjoint_fp64(lib, orc, deg, nc, dim, vbc):
+    s, og = make(lib, orc, deg, nc, vbc=vbc, dt=0.29)
+    lam = random_f(og.shape, seed=300 + dim)
+    gf = random_f(og.shape, seed=400 + dim)
+    frac = 0.5 if dim < 2 else 1.0
+    E = None
+    if dim >= 2:
+        E1 = random_field(og.xshape, seed=11, scale=2.0 * og.h(2) / og.dt)
+        E2 = random_field(og.xshape, seed=12, scale=2.0 * og.h(3) / og.dt)
+        s.set_field(torch.from_numpy(E1), torch.from_numpy(E2))
+        E = E1 if dim == 2 else E2
+    lt = torch.from_numpy(lam.reshape(og.shape)).cuda()
+    if dim >= 2:
+        gt = torch.from_numpy(gf.reshape(og.shape)).cuda()
+        Eb = torch.full(og.xshape, 0.25, dtype=torch.float64, device="cuda")  # accumulates
+        s.sweep_adjoint(dim, frac, lt, gt, Eb)
+        ref, Ebr = orc.sweep_adj(og, dim, lam, Ed=E, frac=frac, gfwd=gf)
+        torch.cuda.synchronize()
+        assert relerr(Eb.cpu().numpy() - 0.25, Ebr) < 1e-12
+    else:
+        s.sweep_adjoint(dim, frac, lt)
+        ref = orc.sweep_adj(og, dim, lam, Ed=E, frac=frac)
+    torch.cuda.synchronize()
+    assert relerr(lt.cpu().numpy(), ref.reshape(og.shape)) < TOL64
+    s.close()
+
+
+@pytest.mark.parametrize("deg,nc,lo,hi", [(1, (6, 5, 7, 8), LANDAU_LO, LANDAU_HI),
+                                          (2, (13, 11, 9, 10), TSI_LO, TSI_HI),
+                                          (3, (5, 7, 4, 4), LANDAU_LO, LANDAU_HI)])
+@pytest.mark.parametrize("kmax", [-1, 3])
+def test_fields(lib, orc, deg, nc, lo, hi, kmax):
+    s, og = make(lib, orc, deg, nc, lo=lo, hi=hi, kmax=kmax)
+    f = random_f(og.shape, seed=5, positive=True)
+    put(s, f)
+    s.compute_fields()
+    rho, E1, E2 = s.fields()
+    r0, F1, F2 = orc.fields(og, f)
+    assert relerr(rho, r0) < TOL64
+    assert relerr(E1, F1) < 1e-12 and relerr(E2, F2) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("kind,params", [(0, (0.5, 0.5, 0.5)), (0, (0.01, 0.5, 0.25)),
+                                         (1, (1e-3, 0.2, 3.0)), (2, (1e-3, 0.2, 2.4))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_initial_values(lib, orc, kind, params, prec):
+    lo, hi = (LANDAU_LO, LANDAU_HI) if kind == 0 else (TSI_LO, TSI_HI)
+    s, og = make(lib, orc, 2, (7, 6, 9, 8), lo=lo, hi=hi, prec=prec)
+    s.set_initial(kind, params)
+    ref = orc.init(og, kind, params).reshape(og.shape)
+    assert relerr(get(s), ref) < (1e-14 if prec == "fp64" else 1e-7)
+    s.close()
+
+
+def test_diagnostics(lib, orc):
+    s, og = make(lib, orc, 2, (7, 6, 9, 8))
+    f = random_f(og.shape, seed=6)
+    put(s, f)
+    d = s.diagnostics()
+    _, E1, E2 = orc.fields(og, f)
+    ref = orc.diagnostics(og, f, E1, E2)
+    for k in ("mass", "l1", "l2sq", "kinetic", "electric", "total"):
+        assert abs(d[k] - ref[k]) <= 1e-13 * max(abs(ref[k]), 1e-300), k
+    s.close()
+
+
+def test_nonfinite_detected(lib, orc):
+    s, og = make(lib, orc, 1, (4, 4, 4, 4))
+    f = random_f(og.shape, seed=7)
+    f.reshape(-1)[123] = np.nan  # injected on the host before upload
+    put(s, f)
+    with pytest.raises(lib.SldgError) as e:
+        s.diagnostics()
+    assert e.value.code == lib._native.SLDG_ERR_NONFINITE
+    s.close()
+
+
+def test_v_sweep_without_field_is_a_state_error(lib, orc):
+    s, og = make(lib, orc, 1, (4, 4, 4, 4))
+    s.set_initial(0, (0.1, 0.5, 0.5))
+    with pytest.raises(lib.SldgError) as e:
+        s.sweep(2, 1.0)
+    assert e.value.code == lib._native.SLDG_ERR_STATE
+    s.close()
+
+
+@pytest.mark.parametrize("deg,nc,dt", [(1, (8, 6, 10, 12), 0.1), (2, (7, 9, 8, 6), 0.05),
+                                       (3, (5, 4, 6, 5), 0.2)])
+@pytest.mark.parametrize("nsteps", [1, 6])
+def test_strang_steps_fp64(lib, orc, deg, nc, dt, nsteps):
+    s, og = make(lib, orc, deg, nc, dt=dt)
+    s.set_initial(0, (0.5, 0.5, 0.5))
+    f0 = orc.init(og, 0, (0.5, 0.5, 0.5))
+    W = s.step(nsteps, history=True)
+    ref, Wr, _, _ = orc.step(og, f0, nsteps)
+    # per step the bound is 1e-12; after several steps report growth within nsteps x bound
+    assert relerr(get(s), ref.reshape(og.shape)) < TOL64_STEP * nsteps
+    assert relerr(W, Wr) < 1e-11
+    s.close()
+
+
+def test_step_from_same_state_each_step(lib, orc):
+    # the per-step bound from identical inputs f^m, for every m of a run
+    s, og = make(lib, orc, 1, (16, 16, 16, 16), dt=0.1)
+    s.set_initial(0, (0.01, 0.5, 0.5))
+    f = orc.init(og, 0, (0.01, 0.5, 0.5))
+    worst = 0.0
+    for m in range(5):
+        put(s, f)
+        s.step(1)
+        f, _, _, _ = orc.step(og, f, 1)
+        worst = max(worst, relerr(get(s), f.reshape(og.shape)))
+    assert worst < TOL64_STEP
+    s.close()
+
+
+def test_fp32_energy_history(lib, orc):
+    # FP32 storage: electric-energy history within 1e-5 of the FP64 oracle
+    s, og = make(lib, orc, 2, (8, 8, 12, 12), dt=0.1, prec="fp32")
+    s.set_initial(0, (0.5, 0.5, 0.5))
+    W = s.step(30, history=True)
+    _, Wr, _, _ = orc.step(og, orc.init(og, 0, (0.5, 0.5, 0.5)), 30)
+    err = np.abs(W - Wr).max() / np.abs(Wr).max()
+    assert err < 1e-5, err
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64"])
+def test_backward_matches_oracle(lib, orc, prec):
+    s, og = make(lib, orc, 1, (6, 5, 8, 7), dt=0.1, prec=prec)
+    params = (0.5, 0.5, 0.5)
+    s.set_initial(0, params)
+    f0 = orc.init(og, 0, params)
+    n, ck = 7, 3
+    W = s.record(n, ck)
+    J, grad = s.backward()
+    Jr, gr, Wr = orc.backward(og, f0, n, ck)
+    assert relerr(W, Wr) < 1e-12
+    assert abs(J - Jr) < 1e-12 * abs(Jr)
+    torch.cuda.synchronize()
+    assert relerr(grad.cpu().numpy(), gr.reshape(og.shape)) < 1e-11
+    # dJ/deps through the library's reduction
+    dfde = orc.init(og, 0, (1.0, 0.5, 0.5)) - orc.init(og, 0, (0.0, 0.5, 0.5))
+    ge = s.initial_param_grad(0, params, grad)
+    assert abs(ge - np.sum(gr * dfde)) < 1e-11 * abs(ge)
+    s.close()
+
+
+def test_autograd_function(lib, orc):
+    from paper_1803_02143_gb300.autograd import time_integrated_energy
+
+    s, og = make(lib, orc, 1, (6, 5, 8, 7), dt=0.1)
+    f0 = torch.from_numpy(orc.init(og, 0, (0.5, 0.5, 0.5)).reshape(og.shape)).cuda()
+    f0.requires_grad_(True)
+    J = time_integrated_energy(f0, s, 5, 2)
+    J.backward()
+    Jr, gr, _ = orc.backward(og, f0.detach().cpu().numpy(), 5, 2)
+    assert abs(J.item() - Jr) < 1e-12 * abs(Jr)
+    assert relerr(f0.grad.cpu().numpy(), gr.reshape(og.shape)) < 1e-11
+    s.close()
+
+
+def test_launch_count_and_timing(lib, orc):
+    s, og = make(lib, orc, 1, (8, 8, 8, 8))
+    s.set_initial(0, (0.1, 0.5, 0.5))
+    s.step(1)
+    n0 = s.launch_count
+    s.timing(True)
+    s.step(2)
+    t = s.timing_read()
+    assert s.launch_count > n0
+    for k in ("x1", "x2", "v1", "v2"):
+        assert t[k][1] >= 2 * (2 if k in ("x1", "x2") else 1) and t[k][0] > 0
+    s.close()
