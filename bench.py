@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true", help="skip the fp32 and adjoint lines")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    p.add_argument("--native-fp64", action="store_true",
+                   help="FP64 storage swept with FP64 FMA instead of double-float arithmetic")
     return p.parse_args()
 
 
@@ -156,7 +159,7 @@ def committed_traffic(key):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline on a bounded slab of the workload
 # ---------------------------------------------------------------------------
-def oracle_slab(w, vcells=16):
+def oracle_slab(w, vcells=32):
     """Same x-grid and degree, v reduced to vcells^2 cells: per-dof work of
     the sweeps is unchanged (same line lengths along x, same degree)."""
     import oracle as orc
@@ -248,7 +251,7 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
     traffic = committed_traffic(f"{w.name}:{cfg.precision}:{kind}")
     hbm = {"achieved": algo_bytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": algo_bytes / avg_s / 1e9 / pk["hbm_gbs"], "peak_source": peak_src}
-    if cfg.precision == "fp64":
+    if cfg.precision == "fp64" and cfg.flags:
         clk = pk.get("sm_max_mhz", 2070.0)
         peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": algo_flops / avg_s / 1e12, "peak": peak_tf,
@@ -362,37 +365,49 @@ def run_ours(args, world, rank, local):
     barrier(world)
     from paper_1803_02143_gb300 import configs
 
-    w = configs.workload(args.workload, args.precision)
+    flags = 1 if args.native_fp64 else 0
+    w = configs.workload(args.workload, args.precision, flags)
     pk, pk_src = peaks()
     s, ms, timing, launches, clocks = run_forward(w, args.steps, args.warmup, world, local)
     ms_max = max_over_ranks(ms, world)
     value = w.cfg.numel * args.steps * world / (ms_max / 1e3)
     roof = sweep_roofline(w, timing, args.steps, pk, pk_src)
-    e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
-    e2e["value"] = e2e["value"] * world
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
+        e2e["value"] = e2e["value"] * world
     s.close()
     del s
     torch.cuda.empty_cache()
     extras = {}
     if not args.no_extras and rank == 0:
-        other = "fp32" if w.cfg.precision == "fp64" else "fp64"
-        w2 = configs.workload(args.workload, other)
-        s2, ms2, t2, _, _ = run_forward(w2, args.steps, args.warmup, 1, local, sample_clocks=False)
-        s2.close()
-        del s2
-        torch.cuda.empty_cache()
-        extras[other] = {"value": w2.cfg.numel * args.steps / (ms2 / 1e3), "unit": UNIT,
-                         "ms_per_step": ms2 / args.steps,
-                         "roofline": sweep_roofline(w2, t2, args.steps, pk, pk_src)}
-        extras["fp32_over_fp64_step_time"] = (
-            (ms2 / ms) if other == "fp32" else (ms / ms2))
+        # the other storage precision, and FP64 storage with FP64-FMA sweeps
+        variants = [("fp32", "fp32", 0), ("fp64_fma", "fp64", 1)]
+        if w.cfg.precision == "fp32":
+            variants = [("fp64", "fp64", 0)]
+        times = {}
+        for name, prec, fl in variants:
+            w2 = configs.workload(args.workload, prec, fl)
+            s2, ms2, t2, _, _ = run_forward(w2, args.steps, args.warmup, 1, local,
+                                            sample_clocks=False)
+            s2.close()
+            del s2
+            torch.cuda.empty_cache()
+            times[name] = ms2
+            extras[name] = {"value": w2.cfg.numel * args.steps / (ms2 / 1e3), "unit": UNIT,
+                            "ms_per_step": ms2 / args.steps,
+                            "roofline": sweep_roofline(w2, t2, args.steps, pk, pk_src)}
+        if "fp32" in times:
+            extras["fp32_over_fp64_step_time"] = times["fp32"] / ms
+        elif "fp64" in times:
+            extras["fp32_over_fp64_step_time"] = ms / times["fp64"]
         extras["adjoint"] = run_adjoint_ratio()
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle as orc
 
         orc.build()
-        cpu = time_oracle(w, nsteps=2)
+        cpu = time_oracle(w, nsteps=5)
         cpu["host"] = cpu_info()
     if rank != 0:
         return
@@ -402,6 +417,8 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if w.cfg.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": w.name, "cells": list(w.cfg.ncell), "degree": w.cfg.degree,
+                   "fp64_sweeps": ("fp64 fma" if w.cfg.flags else "double-float on the fp32 pipe")
+                   if w.cfg.precision == "fp64" else None,
                    "dofs": w.cfg.numel, "dt": w.cfg.dt, "initial": list(w.params),
                    "l2": "inputs larger than L2 (f is %.1f GB)" % (
                        w.cfg.numel * (8 if w.cfg.precision == "fp64" else 4) / 1e9),

@@ -58,6 +58,12 @@ extern "C" {
 #define SLDG_FP32 1 /* f stored and swept in float; matrices built in double and
                        rounded once; rho, Poisson and reductions in double */
 
+/* sldg_config.flags bits */
+#define SLDG_FLAG_NATIVE_FP64 1 /* FP64 storage: sweep with FP64 FMA instead of the
+                                   default double-float arithmetic on the FP32
+                                   pipe (same results to ~1e-15; slower on GB300,
+                                   whose FP64 pipe is about 1/64 of FP32) */
+
 #define SLDG_VBC_ZERO_INFLOW 0 /* v-sweeps drop source cells outside the box */
 #define SLDG_VBC_PERIODIC 1    /* v-sweeps wrap (test mode: exact mass) */
 
@@ -88,7 +94,7 @@ typedef struct {
   int vbc;          /* SLDG_VBC_ZERO_INFLOW or SLDG_VBC_PERIODIC */
   int poisson_kmax; /* Fourier modes |m_d| <= K_d; < 0 selects
                        K_d = min(ncell_d - 1, (D_d - 1) / 2) */
-  int flags;        /* reserved, must be 0 */
+  int flags;        /* 0 or SLDG_FLAG_NATIVE_FP64 */
 } sldg_config;
 
 typedef struct {

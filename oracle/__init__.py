@@ -11,7 +11,7 @@ compiles it with gcc and marshals numpy arrays through ctypes.
 
 Parity pins (see ``tests/test_oracle_*.py``): Gauss-Legendre nodes against
 numpy and closed forms; the projection matrices against exact rational
-integration (sympy), donor-cell upwinding at degree 0, the identity at
+polynomial integration (40-digit mpmath), donor-cell upwinding at degree 0, the identity at
 theta = 0 and 1, the column mass identity and finite differences of their
 theta-derivatives; the sweep against integer-cell permutation, polynomial
 reproduction, mass conservation and the two-cell stencil; the Poisson map
@@ -92,6 +92,7 @@ def _lib_handle():
                                              _DP]),
             "orc_rho": (ctypes.c_int, [G, _DP, _DP]),
             "orc_rho_adj": (ctypes.c_int, [G, _DP, _DP]),
+            "orc_rho_column": (ctypes.c_double, [G, _DP]),
             "orc_poisson": (ctypes.c_int, [G, _DP, _DP, _DP]),
             "orc_poisson_adj": (ctypes.c_int, [G, _DP, _DP, _DP]),
             "orc_electric_energy": (ctypes.c_double, [G, _DP, _DP]),
@@ -260,6 +261,13 @@ def rho(g: Grid, f):
     r = np.zeros(g.xshape)
     _lib_handle().orc_rho(g.c(), _p(f), _p(r))
     return r
+
+
+def rho_column(g: Grid, col):
+    """v-quadrature of one x-node's v-plane col (shape (D_v2, D_v1))."""
+    c = np.ascontiguousarray(col, dtype=np.float64)
+    assert c.size == g.D(2) * g.D(3)
+    return _lib_handle().orc_rho_column(g.c(), _p(c))
 
 
 def rho_adj(g: Grid, rhobar, lam=None):

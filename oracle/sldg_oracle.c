@@ -413,6 +413,21 @@ int orc_rho(const orc_grid* g, const double* f, double* rho) {
   return 0;
 }
 
+/* The same v-quadrature for one x-node whose v-plane col[i3][i2] (D2*D3
+   values, v1 fastest) was gathered out of f. */
+double orc_rho_column(const orc_grid* g, const double* col) {
+  int n = g->deg + 1;
+  double xi[ORC_MAXN], w[ORC_MAXN];
+  long D[4], S[4];
+  orc_gauss_legendre(n, xi, w);
+  strides(g, D, S);
+  ksum k = {0.0, 0.0};
+  for (long i3 = 0; i3 < D[3]; ++i3)
+    for (long i2 = 0; i2 < D[2]; ++i2)
+      kadd(&k, node_weight(g, 2, i2, w) * node_weight(g, 3, i3, w) * col[i3 * D[2] + i2]);
+  return kval(&k);
+}
+
 /* lam[v][x] += (h_v1 w)(h_v2 w) rhobar[x]: the transpose of orc_rho. */
 int orc_rho_adj(const orc_grid* g, const double* rhobar, double* lam) {
   int n = g->deg + 1;

@@ -25,6 +25,7 @@ SLDG_ERR_ARG = -8
 
 SLDG_FP64 = 0
 SLDG_FP32 = 1
+SLDG_FLAG_NATIVE_FP64 = 1
 SLDG_VBC_ZERO_INFLOW = 0
 SLDG_VBC_PERIODIC = 1
 SLDG_INIT_LANDAU = 0

@@ -38,6 +38,10 @@ WORKLOADS = {
     # nonlinear Landau damping, 64^4 cells, degree 2 (1.36e9 dofs), dt 0.05 to T = 20
     "nonlinear_landau_64": Workload("nonlinear_landau_64", _landau(2, 64, 0.05, 0.5),
                                     N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 400),
+    # the same problem at 48^4 cells (4.3e8 dofs: larger than L2, a few GB) for
+    # profiling captures
+    "nonlinear_landau_48": Workload("nonlinear_landau_48", _landau(2, 48, 0.05, 0.5),
+                                    N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 400),
     # two-stream instability, 64^2 x 128^2 cells, degree 2 (5.4e9 dofs), dt 0.05 to T = 40
     "two_stream_64x128": Workload(
         "two_stream_64x128",
@@ -52,10 +56,11 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, precision: str | None = None) -> Workload:
+def workload(name: str, precision: str | None = None, flags: int = 0) -> Workload:
     w = WORKLOADS[name]
-    if precision is None or precision == w.cfg.precision:
+    if (precision is None or precision == w.cfg.precision) and flags == w.cfg.flags:
         return w
     c = w.cfg
-    return Workload(w.name, Config(c.degree, c.ncell, c.lo, c.hi, c.dt, precision, c.vbc,
-                                   c.poisson_kmax), w.kind, w.params, w.steps, w.ckpt)
+    return Workload(w.name, Config(c.degree, c.ncell, c.lo, c.hi, c.dt, precision or c.precision,
+                                   c.vbc, c.poisson_kmax, flags), w.kind, w.params, w.steps,
+                    w.ckpt)

@@ -144,7 +144,7 @@ int validate(const sldg_config* cfg) {
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
   if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
   if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->flags != 0) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & ~SLDG_FLAG_NATIVE_FP64) return SLDG_ERR_BAD_CONFIG;
   return SLDG_OK;
 }
 
@@ -165,8 +165,8 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_wv);
   dfree(c->d_wx);
   for (int d = 0; d < 2; ++d) {
-    dfree(c->xm[d].ab); dfree(c->xm[d].dab); dfree(c->xm[d].s);
-    dfree(c->vm[d].ab); dfree(c->vm[d].dab); dfree(c->vm[d].s);
+    dfree(c->xm[d].ab); dfree(c->xm[d].dab); dfree(c->xm[d].ab2); dfree(c->xm[d].s);
+    dfree(c->vm[d].ab); dfree(c->vm[d].dab); dfree(c->vm[d].ab2); dfree(c->vm[d].s);
     dfree(c->d_E[d]);
     dfree(c->d_Eb[d]);
   }
@@ -199,6 +199,7 @@ int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv) {
   if (!m->ab) {
     SLDG_TRY(dalloc(&m->ab, 2 * nn * count * c->esize));
     SLDG_TRY(dalloc(&m->s, count * sizeof(int)));
+    if (c->prec == SLDG_FP64) SLDG_TRY(dalloc(&m->ab2, 2 * nn * count * sizeof(float2)));
     m->count = count;
   }
   if (deriv && !m->dab) SLDG_TRY(dalloc(&m->dab, 2 * nn * count * c->esize));
@@ -213,7 +214,7 @@ int ensure_xmats(sldg_ctx* c, int d, double frac) {
   SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false));
   KTimer t(c, SLDG_K_VMAT);
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], c->basis,
-                            m.ab, nullptr, m.s, c->stream));
+                            m.ab, nullptr, m.ab2, m.s, c->stream));
   m.frac = frac;
   m.valid = true;
   return SLDG_OK;
@@ -227,7 +228,7 @@ int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv) {
   SLDG_TRY(alloc_matset(c, &m, c->g.Dx, deriv));
   KTimer t(c, SLDG_K_VMAT);
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], c->basis,
-                            m.ab, deriv ? m.dab : nullptr, m.s, c->stream));
+                            m.ab, deriv ? m.dab : nullptr, m.ab2, m.s, c->stream));
   m.frac = frac;
   m.valid = true;
   m.with_deriv = deriv;
@@ -260,7 +261,9 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
     a.periodic = g.vbc == SLDG_VBC_PERIODIC;
   }
   a.ab = m->ab;
+  a.ab2 = m->ab2;
   a.dab = m->dab;
+  a.native_fp64 = (c->cfg.flags & SLDG_FLAG_NATIVE_FP64) ? 1 : 0;
   a.s = m->s;
   a.mcount = m->count;
   switch (dim) {
@@ -297,7 +300,10 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   const int kind = adjoint ? (dim < 2 ? SLDG_K_ADJ_X : SLDG_K_ADJ_V) : SLDG_K_X1 + dim;
   {
     KTimer t(c, kind);
-    cudaError_t e = c->prec == SLDG_FP64 ? launch_sweep_f64(a, c->stream) : launch_sweep_f32(a, c->stream);
+    cudaError_t e;
+    if (c->prec == SLDG_FP32) e = launch_sweep_f32(a, c->stream);
+    else if (a.adjoint || a.native_fp64) e = launch_sweep_f64(a, c->stream);
+    else e = launch_sweep_df(a, c->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return SLDG_ERR_CUDA;

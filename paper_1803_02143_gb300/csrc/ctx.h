@@ -18,6 +18,7 @@ namespace sldg {
 struct MatSet {
   void* ab = nullptr;   // element type of the context precision
   void* dab = nullptr;  // same precision, derivative matrices
+  void* ab2 = nullptr;  // FP64 contexts: (hi, lo) float pairs of ab, same layout
   int* s = nullptr;
   long long count = 0;
   double frac = 0.0;    // shift scale these matrices were built for
@@ -37,6 +38,7 @@ struct SweepArgs {
   long long inner;     // elements between consecutive nodes along dim
   long long outer;     // number of (D x inner) blocks
   const void* ab;      // matrices (SoA), see MatSet
+  const void* ab2;     // the same matrices as (hi, lo) float pairs (FP64 contexts)
   const void* dab;
   const int* s;
   long long mcount;    // keys in the matrix set
@@ -45,10 +47,12 @@ struct SweepArgs {
   int periodic;
   int adjoint;
   int lines_per_tile;  // x1-sweep tile height R (divides D1)
+  int native_fp64;     // FP64 storage: 1 = FP64 FMA kernels, 0 = double-float kernels
 };
 
 // Kernel launchers (sweep_f64.cu / sweep_f32.cu).
-cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);  // FP64 FMA
+cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st);   // double-float
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
 

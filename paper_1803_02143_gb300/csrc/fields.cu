@@ -60,7 +60,8 @@ __device__ void block_ksum(KSum (&k)[M], KSum* shm /* 32*M */) {
 template <typename T>
 __global__ void k_build_mats(long long count, const double* __restrict__ src, double dt,
                              double frac, double h, Basis b, T* __restrict__ ab,
-                             T* __restrict__ dab, int* __restrict__ svec) {
+                             T* __restrict__ dab, float2* __restrict__ ab2,
+                             int* __restrict__ svec) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= count) return;
   const double a = __dmul_rn(__dmul_rn(src[e], dt), frac);
@@ -74,6 +75,11 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
   for (int i = 0; i < nn; ++i) {
     ab[(long long)i * count + e] = (T)A[i];
     ab[(long long)(nn + i) * count + e] = (T)B[i];
+    if (ab2) {  // (hi, lo) split: hi = A rounded to float, lo = the remainder
+      const float ah = (float)A[i], bh = (float)B[i];
+      ab2[(long long)i * count + e] = make_float2(ah, (float)(A[i] - (double)ah));
+      ab2[(long long)(nn + i) * count + e] = make_float2(bh, (float)(B[i] - (double)bh));
+    }
     if (dab) {
       dab[(long long)i * count + e] = (T)dA[i];
       dab[(long long)(nn + i) * count + e] = (T)dB[i];
@@ -456,15 +462,16 @@ __global__ void k_energy_adj(double* __restrict__ Eb1, double* __restrict__ Eb2,
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_build_mats(int prec, long long count, const double* src, double dt, double frac,
-                              double h, const Basis& b, void* ab, void* dab, int* s,
+                              double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
                               cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (prec == SLDG_FP64)
     k_build_mats<double><<<nblk(count, 128), 128, 0, st>>>(count, src, dt, frac, h, b,
-                                                           (double*)ab, (double*)dab, s);
+                                                           (double*)ab, (double*)dab,
+                                                           (float2*)ab2, s);
   else
     k_build_mats<float><<<nblk(count, 128), 128, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
-                                                          (float*)dab, s);
+                                                          (float*)dab, nullptr, s);
   return cudaGetLastError();
 }
 

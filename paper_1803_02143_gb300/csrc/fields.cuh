@@ -14,7 +14,7 @@ struct PoissonArgs {
 };
 
 cudaError_t launch_build_mats(int prec, long long count, const double* src, double dt, double frac,
-                              double h, const Basis& b, void* ab, void* dab, int* s,
+                              double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
                               cudaStream_t st);
 cudaError_t launch_rho(int prec, const void* f, const Grid& g, const double* wv, double* part,
                        int chunks, double* rho, cudaStream_t st, int* nlaunch);

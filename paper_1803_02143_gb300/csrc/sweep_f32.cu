@@ -4,7 +4,7 @@
 namespace sldg {
 
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st) {
-  return launch_sweep_any<float>(a, st);
+  return launch_sweep_any<PolF32>(a, st);
 }
 
 }  // namespace sldg

@@ -1,10 +1,11 @@
-// sweep_f64.cu -- FP64 instantiations of the sweep kernels.
+// sweep_f64.cu -- FP64-FMA instantiations of the sweep kernels (the
+// transposed sweeps of FP64 contexts, and forward sweeps on request).
 #include "sweep_kernels.cuh"
 
 namespace sldg {
 
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st) {
-  return launch_sweep_any<double>(a, st);
+  return launch_sweep_any<PolF64>(a, st);
 }
 
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile) {

@@ -26,6 +26,7 @@ class Config:
     precision: str = "fp64"
     vbc: int = N.SLDG_VBC_ZERO_INFLOW
     poisson_kmax: int = -1
+    flags: int = 0  # N.SLDG_FLAG_NATIVE_FP64: FP64 sweeps with FP64 FMA
 
     def c(self) -> N.sldg_config:
         c = N.sldg_config()
@@ -38,7 +39,7 @@ class Config:
         c.precision = N.SLDG_FP64 if self.precision == "fp64" else N.SLDG_FP32
         c.vbc = int(self.vbc)
         c.poisson_kmax = int(self.poisson_kmax)
-        c.flags = 0
+        c.flags = int(self.flags)
         return c
 
     @property

@@ -1,0 +1,116 @@
+"""Parity at the benchmark's full size (nonlinear Landau damping, 64^4 cells,
+degree 2, 1.36e9 nodal values) in the launch configuration bench.py times.
+
+The oracle cannot step 1.36e9 values, so each stage of the Strang step is
+run alone through the C ABI (the same kernels sldg_step launches) and
+sampled outputs are recomputed one by one by the oracle: whole lines for the
+sweeps (the oracle's 1D advection of the gathered input line with the
+line's own shift), single x-nodes for rho (the oracle's v-quadrature of the
+gathered v-plane), and the full Poisson map of the GPU's rho.
+"""
+import numpy as np
+import pytest
+
+from inputs import LANDAU_HI, LANDAU_LO, rng
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NLINES = 48
+
+
+@pytest.fixture(scope="module")
+def big():
+    """One full-size context at a time (FP64, then FP32), built on demand."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_02143_gb300 import build
+
+    build.build()
+    live = {}
+    yield live
+    for s, _ in live.values():
+        s.close()
+
+
+def _context(big, orc, prec):
+    if prec in big:
+        return big[prec]
+    for s, _ in list(big.values()):
+        s.close()
+    big.clear()
+    import paper_1803_02143_gb300 as P
+    from paper_1803_02143_gb300 import configs
+
+    torch.cuda.empty_cache()
+    w = configs.workload("nonlinear_landau_64", prec)
+    s = P.Sldg(w.cfg)
+    s.set_initial(w.kind, w.params)
+    s.step(1)  # a developed state, not the separable initial value
+    og = orc.Grid(deg=w.cfg.degree, nc=w.cfg.ncell, lo=w.cfg.lo, hi=w.cfg.hi, dt=w.cfg.dt)
+    big[prec] = (s, og)
+    return big[prec]
+
+
+def _lines(F, d, idx):
+    """Gather the lines along direction d at the sampled other-indices."""
+    if d == 0:
+        return F[idx[:, 0], idx[:, 1], idx[:, 2], :]
+    if d == 1:
+        return F[idx[:, 0], idx[:, 1], :, idx[:, 2]]
+    if d == 2:
+        return F[idx[:, 0], :, idx[:, 1], idx[:, 2]]
+    return F[:, idx[:, 0], idx[:, 1], idx[:, 2]].T
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_fullsize_sweep_sampled_lines(big, orc, prec, d):
+    s, og = _context(big, orc, prec)
+    F = s.f
+    shp = og.shape
+    other = [a for a in range(4) if a != 3 - d]  # numpy axes other than d's
+    r = rng(1000 + d)
+    idx = np.stack([r.integers(0, shp[a], NLINES) for a in other], axis=1)
+    idx_t = torch.from_numpy(idx).cuda()
+    if d >= 2:
+        s.compute_fields()
+        _, E1, E2 = s.fields()
+    before = _lines(F, d, idx_t).double().cpu().numpy()
+    frac = 0.5 if d < 2 else 1.0
+    s.sweep(d, frac)
+    torch.cuda.synchronize()
+    after = _lines(F, d, idx_t).double().cpu().numpy()
+    worst = 0.0
+    for k in range(NLINES):
+        # node coordinates / field at this line, from the oracle's grid
+        if d == 0:
+            a = og.nodes(2)[idx[k, 1]] * og.dt * frac        # axes (v2, v1, x2)
+        elif d == 1:
+            a = og.nodes(3)[idx[k, 0]] * og.dt * frac        # axes (v2, v1, x1)
+        elif d == 2:
+            a = E1[idx[k, 1], idx[k, 2]] * og.dt * frac      # axes (v2, x2, x1)
+        else:
+            a = E2[idx[k, 1], idx[k, 2]] * og.dt * frac      # axes (v1, x2, x1)
+        ref = orc.advect_line(og.deg, og.nc[d], og.h(d), a, d < 2, before[k])
+        worst = max(worst, np.abs(after[k] - ref).max() / max(np.abs(ref).max(), 1e-300))
+    assert worst < (1e-13 if prec == "fp64" else 2e-6), worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fullsize_rho_and_poisson(big, orc, prec):
+    s, og = _context(big, orc, prec)
+    s.compute_fields()
+    rho, E1, E2 = s.fields()
+    r = rng(77)
+    F = s.f
+    for _ in range(8):
+        i1, i0 = int(r.integers(0, og.D(1))), int(r.integers(0, og.D(0)))
+        col = F[:, :, i1, i0].double().cpu().numpy()
+        ref = orc.rho_column(og, col)
+        assert abs(rho[i1, i0] - ref) < 1e-13 * abs(ref)
+    # the full Poisson map of the GPU's rho
+    R1, R2 = orc.poisson(og, rho)
+    scale = max(np.abs(R1).max(), np.abs(R2).max())
+    assert np.abs(E1 - R1).max() < 1e-12 * scale and np.abs(E2 - R2).max() < 1e-12 * scale

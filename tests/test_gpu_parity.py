@@ -32,9 +32,10 @@ def lib():
     return P
 
 
-def make(P, orc, deg, nc, lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1, prec="fp64", vbc=0, kmax=-1):
+def make(P, orc, deg, nc, lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1, prec="fp64", vbc=0, kmax=-1,
+         flags=0):
     cfg = P.Config(degree=deg, ncell=nc, lo=lo, hi=hi, dt=dt, precision=prec, vbc=vbc,
-                   poisson_kmax=kmax)
+                   poisson_kmax=kmax, flags=flags)
     og = orc.Grid(deg=deg, nc=nc, lo=lo, hi=hi, dt=dt, vbc=vbc, kmax=kmax)
     return P.Sldg(cfg), og
 
@@ -63,8 +64,9 @@ GRIDS = [
 @pytest.mark.parametrize("deg,nc", GRIDS)
 @pytest.mark.parametrize("dim", [0, 1, 2, 3])
 @pytest.mark.parametrize("vbc", [0, 1])
-def test_sweep_fp64(lib, orc, deg, nc, dim, vbc):
-    s, og = make(lib, orc, deg, nc, vbc=vbc, dt=0.37)
+@pytest.mark.parametrize("flags", [0, 1], ids=["doublefloat", "nativefp64"])
+def test_sweep_fp64(lib, orc, deg, nc, dim, vbc, flags):
+    s, og = make(lib, orc, deg, nc, vbc=vbc, dt=0.37, flags=flags)
     f = random_f(og.shape, seed=100 + dim)
     put(s, f)
     frac = 0.5 if dim < 2 else 1.0
@@ -170,14 +172,22 @@ def test_diagnostics(lib, orc):
     s.close()
 
 
-def test_nonfinite_detected(lib, orc):
-    s, og = make(lib, orc, 1, (4, 4, 4, 4))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_detected(lib, orc, prec, bad):
+    s, og = make(lib, orc, 1, (4, 4, 4, 4), prec=prec)
     f = random_f(og.shape, seed=7)
-    f.reshape(-1)[123] = np.nan  # injected on the host before upload
+    f.reshape(-1)[123] = bad  # injected on the host before upload
     put(s, f)
     with pytest.raises(lib.SldgError) as e:
         s.diagnostics()
     assert e.value.code == lib._native.SLDG_ERR_NONFINITE
+    # the sweeps carry the non-finite value on instead of hiding it
+    s.set_initial(0, (0.1, 0.5, 0.5))
+    put(s, f)
+    s.sweep(0, 0.5)
+    s.sweep(1, 0.5)
+    assert not np.isfinite(get(s)).all()
     s.close()
 
 
@@ -193,8 +203,9 @@ def test_v_sweep_without_field_is_a_state_error(lib, orc):
 @pytest.mark.parametrize("deg,nc,dt", [(1, (8, 6, 10, 12), 0.1), (2, (7, 9, 8, 6), 0.05),
                                        (3, (5, 4, 6, 5), 0.2)])
 @pytest.mark.parametrize("nsteps", [1, 6])
-def test_strang_steps_fp64(lib, orc, deg, nc, dt, nsteps):
-    s, og = make(lib, orc, deg, nc, dt=dt)
+@pytest.mark.parametrize("flags", [0, 1], ids=["doublefloat", "nativefp64"])
+def test_strang_steps_fp64(lib, orc, deg, nc, dt, nsteps, flags):
+    s, og = make(lib, orc, deg, nc, dt=dt, flags=flags)
     s.set_initial(0, (0.5, 0.5, 0.5))
     f0 = orc.init(og, 0, (0.5, 0.5, 0.5))
     W = s.step(nsteps, history=True)
