@@ -17,7 +17,8 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr size_t kMaxSmem = 227 * 1024;
-constexpr size_t kX1TileBudget = 48 * 1024;
+constexpr size_t kX1TileBudget = 48 * 1024;    // FP32 x1 tiles
+constexpr size_t kX1TileBudget64 = 56 * 1024;  // FP64 x1 tiles (two CTAs per SM)
 constexpr int kTimerPairs = 8192;
 
 // ---- Gauss-Legendre basis on [0,1] from the closed-form roots ---------------
@@ -153,7 +154,7 @@ int x1_lines_per_tile(const sldg_ctx* c) {
   int best = 1;
   for (int R = 1; R <= 64 && R <= D1; ++R) {
     if (D1 % R) continue;
-    if (sweep_smem_bytes(c->prec, 0, D0, R) <= kX1TileBudget) best = R;
+    if (sweep_smem_bytes(c->prec, 0, D0, R) <= (c->prec == SLDG_FP64 ? kX1TileBudget64 : kX1TileBudget)) best = R;
   }
   return best;
 }
@@ -163,6 +164,7 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_z[0]);  // coordinates are one allocation
   for (int d = 1; d < 4; ++d) c->d_z[d] = nullptr;
   dfree(c->d_wv);
+  dfree(c->d_wv2);
   dfree(c->d_wx);
   for (int d = 0; d < 2; ++d) {
     dfree(c->xm[d].ab); dfree(c->xm[d].dab); dfree(c->xm[d].ab2); dfree(c->xm[d].s);
@@ -238,8 +240,9 @@ int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv) {
 void invalidate_vmats(sldg_ctx* c) { c->vm[0].valid = c->vm[1].valid = false; }
 
 // ---- sweeps ---------------------------------------------------------------------------
+// in_df / out_df: FP64 double-float sweeps read / write (hi, lo) pairs
 int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const void* gfwd,
-              double* Ebar) {
+              double* Ebar, bool in_df = false, bool out_df = false) {
   const Grid& g = c->g;
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -264,6 +267,8 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   a.ab2 = m->ab2;
   a.dab = m->dab;
   a.native_fp64 = (c->cfg.flags & SLDG_FLAG_NATIVE_FP64) ? 1 : 0;
+  a.in_df = in_df ? 1 : 0;
+  a.out_df = out_df ? 1 : 0;
   a.s = m->s;
   a.mcount = m->count;
   switch (dim) {
@@ -319,11 +324,12 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   return SLDG_OK;
 }
 
-int compute_fields(sldg_ctx* c, const void* buf) {
+int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
   int nl = 0;
   {
     KTimer t(c, SLDG_K_RHO, 2);
-    SLDG_CU(launch_rho(c->prec, buf, c->g, c->d_wv, c->d_part, c->rho_chunks, c->d_rho, c->stream, &nl));
+    SLDG_CU(launch_rho(c->prec, buf, c->g, c->d_wv2, c->d_part, c->rho_chunks, c->d_rho, c->stream,
+                       &nl, df ? 1 : 0));
   }
   {
     KTimer t(c, SLDG_K_POISSON, 4);
@@ -336,18 +342,23 @@ int compute_fields(sldg_ctx* c, const void* buf) {
 }
 
 // One Strang step in place on buf; W(E) of the kick field to Wslot (device) if given.
+// FP64 storage with double-float sweeps: buf holds IEEE doubles before and
+// after the step; the five intermediate sub-step states in between are kept
+// as double-float (hi, lo) pairs in the same 8-byte elements, so the
+// conversion to and from the FP32 pipe's format happens once per step.
 int do_step(sldg_ctx* c, void* buf, double* Wslot) {
-  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr));
-  SLDG_TRY(compute_fields(c, buf));
+  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
+  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
+  SLDG_TRY(compute_fields(c, buf, df));
   if (Wslot) {
     KTimer t(c, SLDG_K_OTHER);
     SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream));
   }
-  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
+  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
+  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
+  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
   return SLDG_OK;
 }
 
@@ -386,6 +397,15 @@ int build_tables(sldg_ctx* c) {
   for (long long i1 = 0; i1 < g.D[1]; ++i1)
     for (long long i0 = 0; i0 < g.D[0]; ++i0) wx[i1 * g.D[0] + i0] = wall[0][i0] * wall[1][i1];
   SLDG_TRY(dalloc(&c->d_wv, g.Dv * sizeof(double)));
+  {
+    std::vector<float2> wv2(g.Dv);
+    for (long long i = 0; i < g.Dv; ++i) {
+      const float h = (float)wv[i];
+      wv2[i] = make_float2(h, (float)(wv[i] - (double)h));
+    }
+    SLDG_TRY(dalloc(&c->d_wv2, g.Dv * sizeof(float2)));
+    SLDG_CU(cudaMemcpy(c->d_wv2, wv2.data(), g.Dv * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   SLDG_TRY(dalloc(&c->d_wx, g.Dx * sizeof(double)));
   SLDG_CU(cudaMemcpy(c->d_wv, wv.data(), g.Dv * sizeof(double), cudaMemcpyHostToDevice));
   SLDG_CU(cudaMemcpy(c->d_wx, wx.data(), g.Dx * sizeof(double), cudaMemcpyHostToDevice));

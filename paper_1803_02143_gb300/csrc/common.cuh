@@ -95,7 +95,8 @@ __host__ __device__ inline void split_shift(double a, double h, int* s, double* 
   const double fl = floor(sigma);
   double th = sigma - fl;
 #endif
-  int si = (int)fl;
+  // shifts beyond 2^30 cells are outside any grid this library accepts
+  int si = (int)fmin(fmax(fl, -1073741824.0), 1073741824.0);
   if (th >= 1.0) {  // sigma a hair below an integer: theta rounded up to 1
     th = 0.0;
     si += 1;

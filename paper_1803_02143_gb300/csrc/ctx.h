@@ -48,6 +48,8 @@ struct SweepArgs {
   int adjoint;
   int lines_per_tile;  // x1-sweep tile height R (divides D1)
   int native_fp64;     // FP64 storage: 1 = FP64 FMA kernels, 0 = double-float kernels
+  int in_df;           // double-float kernels: input elements are (hi, lo) pairs
+  int out_df;          // double-float kernels: write (hi, lo) pairs instead of doubles
 };
 
 // Kernel launchers (sweep_f64.cu / sweep_f32.cu).
@@ -71,6 +73,7 @@ struct sldg_ctx {
   double* d_z[4] = {nullptr, nullptr, nullptr, nullptr};
   double* d_w[4] = {nullptr, nullptr, nullptr, nullptr};
   double* d_wv = nullptr;  // v-plane weights w_v1 * w_v2, Dv doubles
+  float2* d_wv2 = nullptr; // the same weights as (hi, lo) float pairs
   double* d_wx = nullptr;  // x-plane weights w_x1 * w_x2, Dx doubles
 
   sldg::MatSet xm[2];  // x1: key v1 node, x2: key v2 node

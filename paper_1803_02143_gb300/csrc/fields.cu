@@ -3,6 +3,7 @@
 // electric energy, the diagnostics, the initial values and the small adjoint
 // helpers.  Reductions are two-stage with a fixed summation order, so every
 // result is bit-reproducible run to run.
+#include "dfloat.cuh"
 #include "fields.cuh"
 
 namespace sldg {
@@ -92,9 +93,19 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
 // rho(x) = sum_v w_v f[v][x]  (Sec. 2: rho = int g dv, Gauss-Legendre in v).
 // Stage 1: chunk of v-planes per blockIdx.y, one x-node per thread.
 // ---------------------------------------------------------------------------
-template <typename T>
+// Products w_v f are accumulated in double-float on the FP32 pipe (weights
+// as (hi, lo) pairs, FP64 values split with integer operations); every 16
+// terms the double-float partial is flushed into an FP64 sum, so the FP64
+// pipe sees two adds per 16 values and the result keeps FP64 accuracy.
+template <bool DF>
+__device__ __forceinline__ float2 as_pair(float x) { return make_float2(x, 0.0f); }
+template <bool DF>
+__device__ __forceinline__ float2 as_pair(double x) { return DF ? df_unpack(x) : dsplit(x); }
+
+// DF: the FP64 elements hold double-float (hi, lo) pairs
+template <typename T, bool DF>
 __global__ void k_rho_partial(const T* __restrict__ f, long long Dx, long long Dv, long long chunk,
-                              const double* __restrict__ wv, double* __restrict__ part) {
+                              const float2* __restrict__ wv2, double* __restrict__ part) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= Dx) return;
   const long long v0 = blockIdx.y * chunk;
@@ -102,14 +113,28 @@ __global__ void k_rho_partial(const T* __restrict__ f, long long Dx, long long D
   if (v1 > Dv) v1 = Dv;
   double acc = 0.0;
   long long v = v0;
-  for (; v + 8 <= v1; v += 8) {
-    T x[8];
+  for (; v + 16 <= v1; v += 16) {
+    T x[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) x[u] = f[(v + u) * Dx + p];
+    for (int u = 0; u < 16; ++u) x[u] = f[(v + u) * Dx + p];
+    float sh, sl;
+    const float2 w0 = wv2[v];
+    df_first(w0.x, w0.y, as_pair<DF>(x[0]), sh, sl);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = fma(wv[v + u], (double)x[u], acc);
+    for (int u = 1; u < 16; ++u) {
+      const float2 w = wv2[v + u];
+      df_mac(w.x, w.y, as_pair<DF>(x[u]), sh, sl);
+    }
+    acc += djoin(sh, sl);
   }
-  for (; v < v1; ++v) acc = fma(wv[v], (double)f[v * Dx + p], acc);
+  if (v < v1) {
+    float sh = 0.0f, sl = 0.0f;
+    for (; v < v1; ++v) {
+      const float2 w = wv2[v];
+      df_mac(w.x, w.y, as_pair<DF>(f[v * Dx + p]), sh, sl);
+    }
+    acc += djoin(sh, sl);
+  }
   part[blockIdx.y * Dx + p] = acc;
 }
 
@@ -475,14 +500,16 @@ cudaError_t launch_build_mats(int prec, long long count, const double* src, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_rho(int prec, const void* f, const Grid& g, const double* wv, double* part,
-                       int chunks, double* rho, cudaStream_t st, int* nlaunch) {
+cudaError_t launch_rho(int prec, const void* f, const Grid& g, const float2* wv2, double* part,
+                       int chunks, double* rho, cudaStream_t st, int* nlaunch, int df) {
   const long long chunk = (g.Dv + chunks - 1) / chunks;
   dim3 grid(nblk(g.Dx, 256), (unsigned)chunks);
-  if (prec == SLDG_FP64)
-    k_rho_partial<double><<<grid, 256, 0, st>>>((const double*)f, g.Dx, g.Dv, chunk, wv, part);
+  if (prec == SLDG_FP64 && df)
+    k_rho_partial<double, true><<<grid, 256, 0, st>>>((const double*)f, g.Dx, g.Dv, chunk, wv2, part);
+  else if (prec == SLDG_FP64)
+    k_rho_partial<double, false><<<grid, 256, 0, st>>>((const double*)f, g.Dx, g.Dv, chunk, wv2, part);
   else
-    k_rho_partial<float><<<grid, 256, 0, st>>>((const float*)f, g.Dx, g.Dv, chunk, wv, part);
+    k_rho_partial<float, false><<<grid, 256, 0, st>>>((const float*)f, g.Dx, g.Dv, chunk, wv2, part);
   k_sum_rows<<<nblk(g.Dx, 256), 256, 0, st>>>(part, chunks, g.Dx, 1.0, rho, 0);
   *nlaunch += 2;
   return cudaGetLastError();

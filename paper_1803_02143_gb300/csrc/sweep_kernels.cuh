@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "ctx.h"
+#include "dfloat.cuh"
 
 namespace sldg {
 
@@ -62,72 +63,6 @@ __device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
 }
 
 // ---------------------------------------------------------------------------
-// double <-> (hi, lo) float pair with integer operations only
-// ---------------------------------------------------------------------------
-// hi = x truncated to 24 significant bits, lo = the next 23 bits rounded to
-// nearest (|x - hi - lo| <= 2^-47 |x|).  |x| < 2^-126 flushes to zero; Inf and
-// NaN keep their class in hi.
-__device__ __forceinline__ float2 dsplit(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu);
-  const int ef = e - 896;  // float biased exponent of hi
-  const unsigned m23 = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
-  const unsigned hb = sign | ((unsigned)ef << 23) | m23;
-  const unsigned cb = sign | ((unsigned)(ef - 23) << 23);
-  const unsigned lb = (cb | ((lo >> 6) & 0x7FFFFFu)) + ((lo >> 5) & 1u);
-  float h = __uint_as_float(hb);
-  float l = __uint_as_float(lb) - __uint_as_float(cb);
-  if (ef - 23 <= 0) l = 0.0f;
-  if (ef <= 0) h = 0.0f;
-  if (ef >= 255) {  // beyond float range, Inf or NaN
-    h = __uint_as_float(sign | 0x7F800000u | ((e == 0x7FF && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u));
-    l = 0.0f;
-  }
-  return make_float2(h, l);
-}
-
-// Exact float -> double by integer operations (zero, finite and Inf/NaN;
-// float denormals, never produced here above 2^-126 scale, flush to zero).
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned t = u & 0x7FFFFFFFu;
-  unsigned hi = ((t >> 3) + (896u << 20)) | (u & 0x80000000u);
-  unsigned lo = u << 29;
-  if (t < 0x00800000u) {
-    hi = u & 0x80000000u;
-    lo = 0u;
-  }
-  if (t >= 0x7F800000u) hi |= 0x7FF00000u;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ double djoin(float h, float l) { return f2d_bits(h) + f2d_bits(l); }
-
-// Double-float accumulation sum += a * x with a = (ah, al), x = (xh, xl):
-// error-free product of the high parts (FMA), TwoSum into the high word,
-// everything smaller into the low word.
-__device__ __forceinline__ void df_first(float ah, float al, float2 x, float& sh, float& sl) {
-  sh = ah * x.x;
-  sl = fmaf(ah, x.x, -sh);
-  sl = fmaf(ah, x.y, sl);
-  sl = fmaf(al, x.x, sl);
-}
-
-__device__ __forceinline__ void df_mac(float ah, float al, float2 x, float& sh, float& sl) {
-  const float p = ah * x.x;
-  const float e = fmaf(ah, x.x, -p);
-  const float t = sh + p;
-  const float z = t - sh;
-  const float err = (sh - (t - z)) + (p - z);
-  sh = t;
-  sl += err + e;
-  sl = fmaf(ah, x.y, sl);
-  sl = fmaf(al, x.x, sl);
-}
-
-// ---------------------------------------------------------------------------
 // Policies: storage type S, shared tile element E, matrix element M.
 // ---------------------------------------------------------------------------
 struct PolF32 {
@@ -144,13 +79,18 @@ struct PolF64 {
   static constexpr bool kSplit = false;
   __device__ static E conv(S x) { return x; }
 };
-struct PolDF {
+// IN_DF / OUT_DF: the 8-byte elements are read / written as double-float
+// pairs instead of IEEE doubles (sub-steps inside a Strang step).
+template <bool IN_DF, bool OUT_DF>
+struct PolDFT {
   using S = double;
   using E = float2;
   using M = float2;
   static constexpr bool kSplit = true;
-  __device__ static E conv(S x) { return dsplit(x); }
+  __device__ static E conv(S x) { return IN_DF ? df_unpack(x) : dsplit(x); }
+  __device__ static S store(float h, float l) { return OUT_DF ? df_pack(h, l) : djoin(h, l); }
 };
+using PolDF = PolDFT<false, false>;
 
 // y[j] = sum_l M1[j,l] xa[l] + M2[j,l] xb[l] (or the transposes) for one cell.
 template <class P, int N, bool ADJ>
@@ -173,7 +113,7 @@ __device__ __forceinline__ void cell_apply(const typename P::M* A, const typenam
         const float2 b = ADJ ? B[l * N + j] : B[j * N + l];
         df_mac(b.x, b.y, xb[l], sh, sl);
       }
-      y[j] = djoin(sh, sl);
+      y[j] = P::store(sh, sl);
     }
   } else {
 #pragma unroll
@@ -464,10 +404,17 @@ inline int x1_tpl_log2(int nc) {
   return l;
 }
 
+// Opt in to more than 48 KB of dynamic shared memory and ask for the
+// largest shared-memory carveout, so several large tiles fit on one SM.
 template <class KF>
 cudaError_t set_smem(KF kfn, size_t smem) {
-  if (smem > 48 * 1024)
-    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (smem > 16 * 1024)
+    return cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
   return cudaSuccess;
 }
 
