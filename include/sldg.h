@@ -222,6 +222,31 @@ int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
 int sldg_initial_param_grad(sldg_ctx* ctx, int kind, const double* params, int nparams,
                             const void* grad, double* out);
 
+/* ---- allocation-free charge density --------------------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory.  cudaMalloc and cudaFree synchronise the
+ * whole device and take memory outside the caller's own accounting, so code
+ * running in a latency-bound per-step loop, code whose device memory is
+ * owned by another allocator (a framework's caching pool) and code under a
+ * fixed memory budget cannot call them, and sldg_init allocates.
+ *
+ * rho(x) = sum_v w_v f[v][x] of the grid described by cfg (degree, ncell,
+ * lo, hi and precision are read; nothing is kept), f_dev the caller's device
+ * array in the layout of sldg_init, rho_dev the caller's device array of
+ * D_0 D_1 doubles, work issued on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream).  Same values as sldg_compute_fields' rho to
+ * rounding.  No device memory is allocated: the partial sums live in a fixed
+ * 4 MiB array inside the library, held by every device that loads it until
+ * exit.  The first call on each device (with that device current) looks up
+ * that array's device address; make that call before any stream capture.
+ * Nothing has to start at zero: each call writes every partial sum before
+ * it reads it and overwrites all of rho_dev.  Every call reuses the same
+ * array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be ordered by the caller.
+ * Errors: BAD_PTR, BAD_CONFIG, UNSUPPORTED (x-plane D_0 D_1 above 2^19
+ * nodes, or a v-chunk beyond shared memory), CUDA. */
+int sldg_rho_noalloc(const sldg_config* cfg, const void* f_dev, double* rho_dev, void* stream);
+
 /* ---- measurement ---------------------------------------------------------------
  * Kernel launches issued by this context since init (all entry points). */
 long long sldg_launch_count(const sldg_ctx* ctx);

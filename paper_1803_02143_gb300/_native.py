@@ -95,6 +95,7 @@ SIGNATURES = {
     "sldg_record": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     "sldg_backward": (ctypes.c_int, [_VP, _DP, _VP, _DP]),
     "sldg_initial_param_grad": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int, _VP, _DP]),
+    "sldg_rho_noalloc": (ctypes.c_int, [ctypes.POINTER(sldg_config), _VP, _VP, _VP]),
     "sldg_launch_count": (ctypes.c_longlong, [_VP]),
     "sldg_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sldg_timing_read": (ctypes.c_int, [_VP, _DP, _LLP]),
@@ -221,6 +222,11 @@ def sldg_initial_param_grad(ctx, kind: int, params, grad_ptr: int) -> float:
            load().sldg_initial_param_grad(ctx, int(kind), _dptr(p), int(p.size), _VP(grad_ptr),
                                           ctypes.byref(out)))
     return out.value
+
+
+def sldg_rho_noalloc(cfg: sldg_config, f_ptr: int, rho_ptr: int, stream_ptr: int) -> None:
+    _check("sldg_rho_noalloc", load().sldg_rho_noalloc(ctypes.byref(cfg), _VP(f_ptr), _VP(rho_ptr),
+                                                       _VP(stream_ptr)))
 
 
 def sldg_launch_count(ctx) -> int:
