@@ -72,14 +72,22 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The slowest rank's time (a CUDA tensor under NCCL, a CPU one under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, steps, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time."""
+    return units_per_rank * steps * world / (ms_max / 1e3)
 
 
 # ---------------------------------------------------------------------------
@@ -315,7 +323,8 @@ def run_e2e(s, w, steps):
     esize = 8 if s.cfg.precision == "fp64" else 4
     return {"value": s.cfg.numel * steps / (t1 - t0), "unit": UNIT,
             "h2d_bytes_per_step": s.cfg.numel * esize, "d2h_bytes_per_step": 8,
-            "ms_per_step": 1e3 * (t1 - t0) / steps, "last_W": float(np.asarray(W)[0])}
+            "ms_per_step": 1e3 * (t1 - t0) / steps, "steps": steps,
+            "last_W": float(np.asarray(W)[0])}
 
 
 def run_adjoint_ratio():
@@ -370,12 +379,15 @@ def run_ours(args, world, rank, local):
     pk, pk_src = peaks()
     s, ms, timing, launches, clocks = run_forward(w, args.steps, args.warmup, world, local)
     ms_max = max_over_ranks(ms, world)
-    value = w.cfg.numel * args.steps * world / (ms_max / 1e3)
+    value = job_value(w.cfg.numel, args.steps, world, ms_max)
     roof = sweep_roofline(w, timing, args.steps, pk, pk_src)
     e2e = None
     if not args.no_e2e:
+        barrier(world)
         e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
-        e2e["value"] = e2e["value"] * world
+        ms_e2e = max_over_ranks(e2e["ms_per_step"] * e2e["steps"], world)
+        e2e["value"] = job_value(w.cfg.numel, e2e["steps"], world, ms_e2e)
+        e2e["ms_per_step"] = ms_e2e / e2e["steps"]
     s.close()
     del s
     torch.cuda.empty_cache()

@@ -7,6 +7,7 @@ scheme at degree 0, and identities any translate-then-project map satisfies.
 """
 import numpy as np
 import pytest
+from conftest import golden_rows
 
 
 @pytest.mark.parametrize("n", range(1, 9))
@@ -19,15 +20,17 @@ def test_gauss_legendre_matches_numpy(orc, n):
 
 
 def test_gauss_legendre_closed_forms(orc):
-    xi, w = orc.gauss_legendre(1)
-    assert xi[0] == 0.5 and w[0] == 1.0
-    xi, w = orc.gauss_legendre(2)
-    np.testing.assert_allclose(xi, [0.5 - 0.5 / np.sqrt(3), 0.5 + 0.5 / np.sqrt(3)], atol=1e-16)
-    np.testing.assert_allclose(w, [0.5, 0.5], atol=1e-16)
-    xi, w = orc.gauss_legendre(3)
-    r = 0.5 * np.sqrt(3 / 5)
-    np.testing.assert_allclose(xi, [0.5 - r, 0.5, 0.5 + r], atol=1e-16)
-    np.testing.assert_allclose(w, [5 / 18, 8 / 18, 5 / 18], atol=1e-16)
+    import math
+
+    def ev(expr):
+        return eval(expr, {"__builtins__": {}}, {"sqrt": math.sqrt})
+
+    rows = golden_rows("gauss_legendre_01.txt")
+    assert [int(r[0]) for r in rows] == [1, 2, 3, 4]
+    for n, nodes, weights in rows:
+        xi, w = orc.gauss_legendre(int(n))
+        np.testing.assert_allclose(xi, [ev(e) for e in nodes.split(",")], rtol=0, atol=2e-16)
+        np.testing.assert_allclose(w, [ev(e) for e in weights.split(",")], rtol=0, atol=2e-16)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])

@@ -13,6 +13,7 @@
 import numpy as np
 import pytest
 
+from conftest import golden_kv
 from inputs import LANDAU_HI, LANDAU_LO
 
 
@@ -73,8 +74,9 @@ def _dispersion_root(k):
 
 
 def test_dispersion_root_textbook_value():
-    om, ga = _dispersion_root(0.5)
-    assert abs(om - 1.4156) < 1e-3 and abs(ga + 0.1533) < 1e-3
+    ref = golden_kv("landau_dispersion_k05.txt")
+    om, ga = _dispersion_root(ref["k"])
+    assert abs(om - ref["omega_r"]) < ref["abs_tol"] and abs(ga - ref["gamma"]) < ref["abs_tol"]
 
 
 def test_linear_landau_damping_rate(orc):
@@ -110,13 +112,15 @@ def test_mass_conserved_with_periodic_v(orc):
 
 
 def test_nonlinear_landau_energy_error_band(orc):
-    # Sec. 4: energy error of order 1e-3 after the transient at tau = 0.1.
-    g = _grid(orc, 2, (8, 8, 16, 16), dt=0.1)
-    f0 = orc.init(g, orc.LANDAU, [0.5, 0.5, 0.5])
+    # Sec. 4: energy error of order 1e-3 after the transient at tau = 0.1
+    # (on this coarse grid the spatial error adds to it: within 20x the order).
+    ref = golden_kv("nonlinear_landau_energy_error.txt")
+    g = _grid(orc, 2, (8, 8, 16, 16), dt=ref["tau"])
+    f0 = orc.init(g, orc.LANDAU, [ref["eps"], ref["k"], ref["k"]])
     _, E1, E2 = orc.fields(g, f0)
     d0 = orc.diagnostics(g, f0, E1, E2)
     f, _, _, _ = orc.step(g, f0, 40)
     _, E1, E2 = orc.fields(g, f)
     d1 = orc.diagnostics(g, f, E1, E2)
     err = abs(d1["total"] - d0["total"]) / d0["total"]
-    assert err < 2e-2, err
+    assert err < 20 * ref["energy_error_order"], err
