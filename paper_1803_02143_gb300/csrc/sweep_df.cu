@@ -1,8 +1,10 @@
 // sweep_df.cu -- double-float instantiations of the sweep kernels: FP64
 // storage, arithmetic on the FP32 pipe (the forward sweeps of FP64 contexts).
-// The packed FP32x2 kernels (sweep_df2.cuh) take degrees 0..2 on aligned
-// layouts; everything else runs the one-lane double-float kernels.
+// The packed FP32x2 kernels (sweep_df2.cuh for x1, sweep_df3.cuh for the
+// strided directions) take degrees 0..2 on aligned layouts; everything else
+// runs the one-lane double-float kernels.
 #include "sweep_df2.cuh"
+#include "sweep_df3.cuh"
 
 namespace sldg {
 

@@ -319,6 +319,11 @@ __global__ void __launch_bounds__(kX1Threads, 3)
     reinterpret_cast<double2*>(fb)[i] = reinterpret_cast<const double2*>(raw)[i];
 }
 
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st);
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x1_df3_T(const SweepArgs& a, cudaStream_t st);
+
 // Launch the packed kernels when they apply (forward, degree <= 2, aligned
 // layout, even x1 tile height); returns cudaErrorNotSupported otherwise.
 template <int N, bool IN_DF, bool OUT_DF>
@@ -328,6 +333,10 @@ cudaError_t launch_sweep_df2_T(const SweepArgs& a, cudaStream_t st) {
   const long long D = (long long)a.nc * N;
   if (a.adjoint || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
   if (a.dim == 0) {
+    {
+      const cudaError_t e3 = launch_x1_df3_T<N, IN_DF, OUT_DF>(a, st);
+      if (e3 != cudaErrorNotSupported) return e3;
+    }
     const int R = a.lines_per_tile;
     if (R % 2) return cudaErrorNotSupported;
     const size_t smem = x1_df2_smem(D, R, N);
@@ -339,6 +348,10 @@ cudaError_t launch_sweep_df2_T(const SweepArgs& a, cudaStream_t st) {
     return cudaGetLastError();
   }
   if (a.inner % 2) return cudaErrorNotSupported;
+  {
+    const cudaError_t e3 = launch_strided_df3_T<N, IN_DF, OUT_DF>(a, st);
+    if (e3 != cudaErrorNotSupported) return e3;
+  }
   const size_t smem = strided_df2_smem(D, N);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   const long long ncolblk = (a.inner + kStridedW - 1) / kStridedW;

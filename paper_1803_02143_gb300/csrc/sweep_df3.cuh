@@ -1,0 +1,428 @@
+// sweep_df3.cuh -- strided forward sweeps (x2, v1, v2) of FP64 storage in
+// packed double-float arithmetic, organised to keep the instruction count
+// per nodal value low:
+//   - a CTA owns a column block of 32 columns and walks several outer
+//     indices (tiles) with it, so the per-column matrices of the v-sweeps
+//     are staged once per CTA;
+//   - thread (q, g) owns the column pair 2q, 2q+1 (the two lanes of every
+//     FP32x2 instruction) and a run of consecutive cells, so each source
+//     cell is read from shared memory and converted once (the b-cell of
+//     output c is the a-cell of output c+1);
+//   - the staged tile keeps the raw 8-byte elements; there is no separate
+//     conversion pass, and outputs go straight to global memory as double2.
+// All index arithmetic inside a tile is 32-bit.
+#pragma once
+
+#include "sweep_df2.cuh"
+
+namespace sldg {
+
+constexpr int kDf3Threads = 256;
+constexpr int kDf3Pairs = kStridedW / 2;             // 16 column pairs
+constexpr int kDf3Groups = kDf3Threads / kDf3Pairs;  // 16 cell runs
+constexpr int kDf3TilesPerCta = 4;                   // outer indices walked by one CTA
+
+// float4 entries per lane pair: odd, so the 16 pairs' matrix reads of a
+// quarter warp fall in distinct banks
+template <int N>
+__host__ __device__ constexpr int df3_mat_stride() {
+  return 2 * N * N + 1;
+}
+
+template <int N, bool PERCOL>
+inline size_t strided_df3_smem(long long D) {
+  const size_t mats = PERCOL ? (size_t)kDf3Pairs * df3_mat_stride<N>() : (size_t)(2 * N * N);
+  return mats * sizeof(float4) + (size_t)(D + N) * kStridedW * sizeof(double);
+}
+
+// Tile conversion in place: each 16-byte column pair of a staged row,
+// (x_c0, x_c0+1) as IEEE doubles or packed double-float elements, becomes
+// (h_c0, h_c0+1, l_c0, l_c0+1), so that lane-packed operands load directly
+// into register pairs.
+template <bool IN_DF>
+__device__ __forceinline__ void df3_pair_planar(double* __restrict__ raw, int chunks) {
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+    float4* p = reinterpret_cast<float4*>(raw) + i;
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    float h0, l0, h1, l1;
+    load_pair<IN_DF>(v.x, h0, l0);
+    load_pair<IN_DF>(v.y, h1, l1);
+    *p = make_float4(h0, h1, l0, l1);
+  }
+}
+
+// Source cell of both lanes from a pair-planar tile.  SAME: both lanes read
+// cell k0 (one 16-byte load per node).  Else lane 0 reads cell k0 and lane 1
+// cell k1 (per-column shifts that differ across the pair).
+template <int N, bool SAME>
+__device__ __forceinline__ void df3_load_cell(const double* __restrict__ raw, int c0, int k0, int k1,
+                                              float2* xh, float2* xl) {
+  constexpr int W = kStridedW;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float4 u0 = *reinterpret_cast<const float4*>(raw + (k0 * N + l) * W + c0);
+    if (SAME) {
+      xh[l] = make_float2(u0.x, u0.y);
+      xl[l] = make_float2(u0.z, u0.w);
+    } else {
+      const float4 u1 = *reinterpret_cast<const float4*>(raw + (k1 * N + l) * W + c0);
+      xh[l] = make_float2(u0.x, u1.y);
+      xl[l] = make_float2(u0.z, u1.w);
+    }
+  }
+}
+
+// One output cell for both lanes: y = A xa + B xb, stored as double2 rows
+// out[j * rstride].  An empty asm with a memory clobber before each output row
+// keeps its matrix reads next to their use (loading all 2N^2 float4 entries
+// of a cell up front would spill).
+template <int N, bool OUT_DF>
+__device__ __forceinline__ void df3_cell(const float4* __restrict__ M, const float2* ah,
+                                         const float2* al, const float2* bh, const float2* bl,
+                                         double* out, long long rstride) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    asm volatile("" ::: "memory");
+    float2 sh, sl;
+    float4 m = M[j * N];
+    df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[0], al[0], sh, sl);
+#pragma unroll
+    for (int l = 1; l < N; ++l) {
+      m = M[j * N + l];
+      df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[l], al[l], sh, sl);
+    }
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      m = M[N * N + j * N + l];
+      df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), bh[l], bl[l], sh, sl);
+    }
+    *reinterpret_cast<double2*>(out + j * rstride) =
+        make_double2(store_pair<OUT_DF>(sh.x, sl.x), store_pair<OUT_DF>(sh.y, sl.y));
+  }
+}
+
+// Outputs cb .. ce-1 of one column pair: a sliding window over the source
+// cells (the b-cell of output c is the a-cell of output c + 1).  Source cells
+// step along the line with a periodic wrap, or map to the zero cell nc
+// outside a zero-inflow box.
+template <int N, bool PERIODIC, bool SAME, bool OUT_DF>
+__device__ __forceinline__ void df3_run(const double* __restrict__ raw, const float4* __restrict__ M,
+                                        int c0, int cb, int ce, int sa0, int sa1, int nc,
+                                        double* fb, long long rstride) {
+  int k0 = cb + sa0, k1 = cb + sa1;
+  if (PERIODIC) {
+    if (k0 >= nc) k0 -= nc;
+    if (k1 >= nc) k1 -= nc;
+  }
+  auto next = [nc](int k) {
+    if (PERIODIC) return k + 1 == nc ? 0 : k + 1;
+    return k + 1;
+  };
+  auto row = [nc](int k) {
+    if (PERIODIC) return k;
+    return (unsigned)k < (unsigned)nc ? k : nc;
+  };
+  float2 uh[N], ul[N], wh[N], wl[N];
+  df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), uh, ul);
+  double* out = fb + c0 + (long long)cb * N * rstride;
+  const long long cstep = (long long)N * rstride;
+#pragma unroll 1
+  for (int c = cb; c < ce; ++c, out += cstep) {
+    k0 = next(k0);
+    k1 = next(k1);
+    df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), wh, wl);
+    df3_cell<N, OUT_DF>(M, uh, ul, wh, wl, out, rstride);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      uh[l] = wh[l];
+      ul[l] = wl[l];
+    }
+  }
+}
+
+// A tile is 32 of the ncols columns of one outer index o, all D rows:
+// element (o, row r, column c) sits at o * ostride + r * rstride + c.
+// PERCOL (v-sweeps): matrix and shift per column (key = column, the
+// x-node), periodic or zero inflow; consecutive outer indices of a CTA share
+// its matrices.  Else (x2-sweep, periodic): one matrix per tile, key =
+// (o / key_div) % key_mod.
+// Three CTAs per SM: at most 80 registers per thread, and 54 KB of shared
+// memory per CTA for 192-node lines.
+template <int N, bool PERIODIC, bool PERCOL, bool IN_DF, bool OUT_DF>
+__global__ void __launch_bounds__(kDf3Threads, 3)
+    k_sweep_strided_df3(double* __restrict__ f, int ncols, long long rstride, long long ostride,
+                        int nc, int outer, const float2* __restrict__ ab2,
+                        const int* __restrict__ svec, long long mcount, int key_div, int key_mod) {
+  static_assert(PERCOL || PERIODIC, "the per-tile matrix form serves the periodic x2 sweep");
+  constexpr int W = kStridedW;
+  constexpr int MN = 2 * N * N;
+  constexpr int MS = PERCOL ? df3_mat_stride<N>() : MN;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* smat = reinterpret_cast<float4*>(smraw);
+  double* raw =
+      reinterpret_cast<double*>(smraw + (size_t)(PERCOL ? kDf3Pairs * MS : MN) * sizeof(float4));
+  const int D = nc * N;
+  const int col0 = blockIdx.x * W;
+  const int nvalid = min(W, ncols - col0);
+  const int q = threadIdx.x % kDf3Pairs, g = threadIdx.x / kDf3Pairs;
+  const int c0 = 2 * q;
+  const int cb = (g * nc) / kDf3Groups, ce = ((g + 1) * nc) / kDf3Groups;
+  const bool active = c0 < nvalid && cb < ce;
+
+  // a-cell offset per lane: the source a-cell of output c is c + sa
+  // (periodic: sa in [0, nc) and the sum taken mod nc)
+  int sa0 = 0, sa1 = 0;
+  if (PERCOL) {
+    for (int e = threadIdx.x; e < kDf3Pairs * MN; e += blockDim.x) {
+      const int pq = e / MN, i = e - pq * MN;
+      const int k0 = min(col0 + 2 * pq, ncols - 1), k1 = min(col0 + 2 * pq + 1, ncols - 1);
+      const float2 a0 = ab2[(long long)i * mcount + k0], a1 = ab2[(long long)i * mcount + k1];
+      smat[pq * MS + i] = make_float4(a0.x, a1.x, a0.y, a1.y);
+    }
+    sa0 = -svec[min(col0 + c0, ncols - 1)] - 1;
+    sa1 = -svec[min(col0 + c0 + 1, ncols - 1)] - 1;
+    if (PERIODIC) {
+      sa0 = wrap_cell(sa0, nc);
+      sa1 = wrap_cell(sa1, nc);
+    }
+  }
+  if (!PERIODIC)  // the zero cell, rows D .. D+N-1 (never written by tile loads)
+    for (int i = threadIdx.x; i < N * W; i += blockDim.x) raw[D * W + i] = 0.0;
+  const float4* M = PERCOL ? smat + q * MS : smat;
+  const int chunks = D * (W / 2);  // 16-byte chunks of a full tile
+  const int vchunks = nvalid / 2;  // valid chunks per row
+
+  for (int o = blockIdx.y; o < outer; o += gridDim.y) {
+    double* fb = f + (long long)o * ostride + col0;
+    if (!PERCOL) {
+      const int key = (o / key_div) % key_mod;
+      for (int i = threadIdx.x; i < MN; i += blockDim.x) {
+        const float2 a = ab2[(long long)i * mcount + key];
+        smat[i] = make_float4(a.x, a.x, a.y, a.y);
+      }
+      sa0 = wrap_cell(-svec[key] - 1, nc);
+      sa1 = sa0;
+    }
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+      const int r = i / (W / 2), cq = i - r * (W / 2);
+      if (cq < vchunks) cp_async16(raw + r * W + 2 * cq, fb + r * rstride + 2 * cq);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    df3_pair_planar<IN_DF>(raw, D * (W / 2));
+    __syncthreads();
+
+    if (active) {
+      if (sa0 == sa1) df3_run<N, PERIODIC, true, OUT_DF>(raw, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
+      else df3_run<N, PERIODIC, false, OUT_DF>(raw, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
+    }
+    __syncthreads();  // the tile (and a per-tile matrix) is rewritten next
+  }
+}
+
+// Strided sweeps in the (ncols, rstride, ostride, outer) form:
+//   x2: ncols = D0, rows stride D0, outer = v-planes (D2 D3), stride D0 D1;
+//   v1: ncols = Dx, rows stride Dx, outer = D3, stride Dx D2;
+//   v2: ncols = Dx, rows stride Dx D2, outer = D2 (the v1 index), stride Dx.
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st) {
+  double* f = reinterpret_cast<double*>(a.f);
+  const float2* ab2 = reinterpret_cast<const float2*>(a.ab2);
+  const long long D = (long long)a.nc * N;
+  const bool percol = a.dim >= 2;
+  if (!percol && !a.periodic) return cudaErrorNotSupported;
+  long long ncols, rstride, ostride, outer;
+  if (a.dim == 3) {
+    ncols = a.key_mod;
+    rstride = a.inner;
+    ostride = a.key_mod;
+    outer = a.inner / a.key_mod;
+  } else {
+    ncols = a.inner;
+    rstride = a.inner;
+    ostride = D * a.inner;
+    outer = a.outer;
+  }
+  if (percol && ncols != a.key_mod) return cudaErrorNotSupported;
+  if ((ncols | rstride | ostride) & 1) return cudaErrorNotSupported;  // 16-byte column pairs
+  if (ncols > 0x7fffffffLL - kStridedW || outer > 0x7fffffffLL || a.key_div > 0x7fffffffLL ||
+      a.key_mod > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
+    return cudaErrorNotSupported;
+  const long long ncolblk = (ncols + kStridedW - 1) / kStridedW;
+  long long gy = (outer + kDf3TilesPerCta - 1) / kDf3TilesPerCta;
+  if (gy > 65535) gy = 65535;
+  const dim3 grid((unsigned)ncolblk, (unsigned)gy);
+  using KFn = decltype(&k_sweep_strided_df3<N, true, true, IN_DF, OUT_DF>);
+  KFn kfn;
+  size_t smem;
+  if (!percol) {
+    kfn = k_sweep_strided_df3<N, true, false, IN_DF, OUT_DF>;
+    smem = strided_df3_smem<N, false>(D);
+  } else {
+    kfn = a.periodic ? k_sweep_strided_df3<N, true, true, IN_DF, OUT_DF>
+                     : k_sweep_strided_df3<N, false, true, IN_DF, OUT_DF>;
+    smem = strided_df3_smem<N, true>(D);
+  }
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  kfn<<<grid, kDf3Threads, smem, st>>>(f, (int)ncols, rstride, ostride, a.nc, (int)outer, ab2, a.s,
+                                       a.mcount, (int)a.key_div, (int)a.key_mod);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// x1 forward sweep, FP64 storage, packed double-float.  A tile is R (even)
+// consecutive lines with one matrix pair; lines 2p and 2p+1 are the two
+// lanes.  A CTA walks kX1Df3TilesPerCta tiles and loads tile t+1 (cp.async)
+// while it computes tile t:
+//   wait for tile t; stage its matrix                     | barrier
+//   convert raw t into line-pair planes ph, pl ([R/2][D]) | barrier
+//   start loading tile t+1 into the other raw buffer
+//   outputs of tile t into raw t (already converted)      | barrier
+//   store raw t contiguously
+// Thread (p, t): line pair p, cells [cb, ce) of it (a sliding window over
+// the source cells, as in the strided kernel).
+// ---------------------------------------------------------------------------
+constexpr int kX1Df3Threads = 256;
+constexpr int kX1Df3TilesPerCta = 8;
+constexpr size_t kX1Df3SmemBudget = 75 * 1024;  // three CTAs per SM
+
+template <int N>
+inline size_t x1_df3_smem(long long D, int R) {
+  return (size_t)(2 * N * N) * sizeof(float4) + 3 * (size_t)R * D * sizeof(double);
+}
+
+template <int N, bool IN_DF, bool OUT_DF>
+__global__ void __launch_bounds__(kX1Df3Threads, 3)
+    k_sweep_x1_df3(double* __restrict__ f, int nc, int R, int tpp_log2, long long ntiles,
+                   const float2* __restrict__ ab2, const int* __restrict__ svec, long long mcount,
+                   int key_div, int key_mod) {
+  constexpr int MN = 2 * N * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* smat = reinterpret_cast<float4*>(smraw);
+  const int D = nc * N;
+  const int TL = R * D;  // doubles per tile
+  double* rawb[2];
+  rawb[0] = reinterpret_cast<double*>(smraw + MN * sizeof(float4));
+  rawb[1] = rawb[0] + TL;
+  float2* ph = reinterpret_cast<float2*>(rawb[1] + TL);
+  float2* pl = ph + TL / 2;
+  const int TPP = 1 << tpp_log2;  // threads per line pair
+  const int p = threadIdx.x >> tpp_log2, t = threadIdx.x & (TPP - 1);
+  const int cpt = (nc + TPP - 1) >> tpp_log2;
+  const int cb = min(t * cpt, nc), ce = min(cb + cpt, nc);
+  const long long tile0 = (long long)blockIdx.x * kX1Df3TilesPerCta;
+  const long long tile1 = min(tile0 + kX1Df3TilesPerCta, ntiles);
+  const int chunks = TL / 2;
+
+  auto issue = [&](long long tile, double* dst) {
+    const double* src = f + tile * TL;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  issue(tile0, rawb[0]);
+  int b = 0;
+  for (long long tile = tile0; tile < tile1; ++tile, b ^= 1) {
+    double* cur = rawb[b];
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const int key = (int)(((tile * R) / key_div) % key_mod);
+    for (int i = threadIdx.x; i < MN; i += blockDim.x) {
+      const float2 a = ab2[(long long)i * mcount + key];
+      smat[i] = make_float4(a.x, a.x, a.y, a.y);
+    }
+    const int sa = wrap_cell(-svec[key] - 1, nc);
+    __syncthreads();
+    {  // line-pair planes: ph[p][k] = (hi of line 2p, hi of line 2p+1), pl likewise
+      const double* la = cur + (2 * p) * D;
+      for (int k = t; k < D; k += TPP) {
+        float h0, l0, h1, l1;
+        load_pair<IN_DF>(la[k], h0, l0);
+        load_pair<IN_DF>(la[D + k], h1, l1);
+        ph[p * D + k] = make_float2(h0, h1);
+        pl[p * D + k] = make_float2(l0, l1);
+      }
+    }
+    __syncthreads();
+    if (tile + 1 < tile1) issue(tile + 1, rawb[b ^ 1]);
+    if (cb < ce) {
+      const float2* rh = ph + p * D;
+      const float2* rl = pl + p * D;
+      double* oa = cur + (2 * p) * D;
+      int ka = cb + sa;
+      if (ka >= nc) ka -= nc;
+      float2 ah[N], al[N], bh[N], bl[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        ah[l] = rh[ka * N + l];
+        al[l] = rl[ka * N + l];
+      }
+#pragma unroll 1
+      for (int c = cb; c < ce; ++c) {
+        const int kb = ka + 1 == nc ? 0 : ka + 1;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          bh[l] = rh[kb * N + l];
+          bl[l] = rl[kb * N + l];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          asm volatile("" ::: "memory");
+          float2 sh, sl;
+          float4 m = smat[j * N];
+          df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[0], al[0], sh, sl);
+#pragma unroll
+          for (int l = 1; l < N; ++l) {
+            m = smat[j * N + l];
+            df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[l], al[l], sh, sl);
+          }
+#pragma unroll
+          for (int l = 0; l < N; ++l) {
+            m = smat[N * N + j * N + l];
+            df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), bh[l], bl[l], sh, sl);
+          }
+          oa[c * N + j] = store_pair<OUT_DF>(sh.x, sl.x);
+          oa[D + c * N + j] = store_pair<OUT_DF>(sh.y, sl.y);
+        }
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          ah[l] = bh[l];
+          al[l] = bl[l];
+        }
+        ka = kb;
+      }
+    }
+    __syncthreads();
+    double2* dst = reinterpret_cast<double2*>(f + tile * TL);
+    const double2* src = reinterpret_cast<const double2*>(cur);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+// x1 tiles: the largest even power-of-two R <= 32 that divides D1 (tiles
+// never straddle two v1 nodes) and fits the shared-memory budget.
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x1_df3_T(const SweepArgs& a, cudaStream_t st) {
+  double* f = reinterpret_cast<double*>(a.f);
+  const long long D = (long long)a.nc * N;
+  int R = 0;
+  for (int r = 2; r <= 32; r *= 2)
+    if (a.key_div % r == 0 && x1_df3_smem<N>(D, r) <= kX1Df3SmemBudget) R = r;
+  if (R == 0 || a.key_div > 0x7fffffffLL || a.key_mod > 0x7fffffffLL || R * D > 0x7fffffffLL)
+    return cudaErrorNotSupported;
+  int tpp_log2 = 0;
+  while ((kX1Df3Threads >> tpp_log2) > R / 2) ++tpp_log2;  // (R/2) << tpp_log2 == threads
+  const long long ntiles = a.outer / R;
+  const long long blocks = (ntiles + kX1Df3TilesPerCta - 1) / kX1Df3TilesPerCta;
+  if (blocks > 0x7fffffffLL) return cudaErrorNotSupported;
+  const size_t smem = x1_df3_smem<N>(D, R);
+  auto kfn = k_sweep_x1_df3<N, IN_DF, OUT_DF>;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  kfn<<<(unsigned)blocks, kX1Df3Threads, smem, st>>>(f, a.nc, R, tpp_log2, ntiles,
+                                                     reinterpret_cast<const float2*>(a.ab2), a.s,
+                                                     a.mcount, (int)a.key_div, (int)a.key_mod);
+  return cudaGetLastError();
+}
+
+}  // namespace sldg
