@@ -198,6 +198,13 @@ def time_oracle(w, nsteps, warmup=0):
 
 def cpu_info():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as fh:
             txt = fh.read()
         for key in ("model name", "CPU part"):
