@@ -202,8 +202,9 @@ int sldg_sweep_adjoint(sldg_ctx* ctx, int dim, double frac, void* lam, const voi
                        double* Ebar);
 
 /* Run nsteps Strang steps from the current f like sldg_step while keeping a
- * checkpoint of f every ckpt_every steps in a library-owned device pool, and
- * record W of each step (W_history, host, nullable).  Prepares sldg_backward.
+ * checkpoint of f every ckpt_every steps in a library-owned device pool
+ * (ceil(nsteps / ckpt_every) copies of f), and record W of each step
+ * (W_history, host, nullable).  Prepares sldg_backward.
  * Errors: ARG, OOM (the pool does not fit), CUDA. */
 int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
 
@@ -212,8 +213,25 @@ int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
  * (the time-integrated electric energy for c_m = dt) with respect to every
  * nodal value of the recorded initial f, written to grad (device, N elements
  * of the context precision).  J_out (host, nullable) receives J.  f is left
- * at the recorded final state.  Errors: STATE (no record), BAD_PTR, OOM. */
+ * at the recorded final state.
+ * Memory: besides the checkpoint pool, two copies of f for the forward
+ * intermediates of one step and up to ckpt_every - 1 recomputation slots
+ * (copies of f), as many as fit in the free device memory less a margin
+ * (and at most the limit of sldg_set_slot_limit).  With every slot a segment
+ * is recomputed once; with fewer, the segment is bisected recursively and
+ * its states are recomputed about log2(ckpt_every) times; with one slot,
+ * from the checkpoint for every step.  The gradient is the same whatever
+ * the number of slots (the same arithmetic, only repeated).
+ * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits), CUDA. */
 int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
+
+/* Upper bound on the recomputation slots of sldg_backward (0 = as many as a
+ * segment can use and the device has room for).  Errors: BAD_PTR, ARG. */
+int sldg_set_slot_limit(sldg_ctx* ctx, int max_slots);
+
+/* Strang steps recomputed by the last sldg_backward and the slots it held
+ * (either pointer nullable).  Errors: BAD_PTR. */
+int sldg_backward_stats(const sldg_ctx* ctx, long long* recomputed_steps, int* slots);
 
 /* sum_n grad[n] * d f0[n] / d params[0] for an initial value of kind
  * SLDG_INIT_* (the derivative with respect to the perturbation amplitude),

@@ -94,6 +94,8 @@ SIGNATURES = {
     "sldg_sweep_adjoint": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP]),
     "sldg_record": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
     "sldg_backward": (ctypes.c_int, [_VP, _DP, _VP, _DP]),
+    "sldg_set_slot_limit": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sldg_backward_stats": (ctypes.c_int, [_VP, _LLP, ctypes.POINTER(ctypes.c_int)]),
     "sldg_initial_param_grad": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int, _VP, _DP]),
     "sldg_rho_noalloc": (ctypes.c_int, [ctypes.POINTER(sldg_config), _VP, _VP, _VP]),
     "sldg_launch_count": (ctypes.c_longlong, [_VP]),
@@ -211,6 +213,17 @@ def sldg_backward(ctx, cW, grad_ptr: int) -> float:
     J = ctypes.c_double(0.0)
     _check("sldg_backward", load().sldg_backward(ctx, _dptr(cW), _VP(grad_ptr), ctypes.byref(J)))
     return J.value
+
+
+def sldg_set_slot_limit(ctx, max_slots: int) -> None:
+    _check("sldg_set_slot_limit", load().sldg_set_slot_limit(ctx, int(max_slots)))
+
+
+def sldg_backward_stats(ctx):
+    n = ctypes.c_longlong(0)
+    k = ctypes.c_int(0)
+    _check("sldg_backward_stats", load().sldg_backward_stats(ctx, ctypes.byref(n), ctypes.byref(k)))
+    return n.value, k.value
 
 
 def sldg_initial_param_grad(ctx, kind: int, params, grad_ptr: int) -> float:

@@ -692,20 +692,15 @@ int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   if (nsteps < 1 || ckpt_every < 1) return SLDG_ERR_ARG;
   const size_t fb = c->g.N * c->esize;
   const size_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
-  const size_t seg = std::min(ckpt_every, nsteps);
   dfree(c->d_ckpool);
   dfree(c->d_seg);
   for (int i = 0; i < 2; ++i) dfree(c->d_work[i]);
   dfree(c->d_Wrec);
+  c->seg_count = 0;
   c->recorded = false;
   SLDG_TRY(dalloc(&c->d_ckpool, nck * fb));
-  SLDG_TRY(dalloc(&c->d_seg, seg * fb));
-  SLDG_TRY(dalloc(&c->d_work[0], fb));
-  SLDG_TRY(dalloc(&c->d_work[1], fb));
   SLDG_TRY(dalloc(&c->d_Wrec, nsteps * sizeof(double)));
-  SLDG_TRY(ensure_adjoint_scratch(c));
   c->ck_count = nck;
-  c->seg_count = seg;
   c->rec_t0 = c->t;
   c->rec_step0 = c->step;
   for (int m = 0; m < nsteps; ++m) {
@@ -728,6 +723,121 @@ int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   return SLDG_OK;
 }
 
+int sldg_set_slot_limit(sldg_ctx* c, int max_slots) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (max_slots < 0) return SLDG_ERR_ARG;
+  c->slot_limit = max_slots;
+  return SLDG_OK;
+}
+
+int sldg_backward_stats(const sldg_ctx* c, long long* recomputed_steps, int* slots) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (recomputed_steps) *recomputed_steps = c->bwd_recomputed;
+  if (slots) *slots = (int)c->seg_count;
+  return SLDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Adjoint of Strang step m (global index) from its initial state fm:
+// grad <- (step m)^T grad + dJ/dW_m c_m contributions (Eq. AB-sldg transposed,
+// the v-shift derivatives, the Poisson and charge-density adjoints).
+int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad) {
+  const Grid& g = c->g;
+  const size_t fb = g.N * c->esize;
+  void* g2 = c->d_work[0];
+  void* g3 = c->d_work[1];
+  // forward intermediates: g2 = X2 X1 f^m (input of V1), g3 = V1 g2 (input of V2)
+  SLDG_CU(cudaMemcpyAsync(g2, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
+  SLDG_TRY(run_sweep(c, g2, 0, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, g2, 1, 0.5, false, nullptr, nullptr));
+  SLDG_TRY(compute_fields(c, g2));
+  SLDG_CU(cudaMemcpyAsync(g3, g2, fb, cudaMemcpyDeviceToDevice, c->stream));
+  SLDG_TRY(run_sweep(c, g3, 2, 1.0, false, nullptr, nullptr));
+  // reverse
+  SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
+  SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
+  SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1]));
+  SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0]));
+  {
+    KTimer t(c, SLDG_K_OTHER);
+    SLDG_CU(launch_energy_adj(c->d_Eb[0], c->d_Eb[1], c->d_E[0], c->d_E[1], c->d_wx, g.Dx,
+                              cW ? cW[m] : g.dt, c->stream));
+  }
+  {
+    int nl = 0;
+    KTimer t(c, SLDG_K_POISSON, 4);
+    SLDG_CU(launch_poisson_adj(poisson_args(c), c->d_Eb[0], c->d_Eb[1], c->d_rhob, c->stream, &nl));
+  }
+  {
+    KTimer t(c, SLDG_K_RHO);
+    SLDG_CU(launch_rho_adj(c->prec, grad, g, c->d_wv, c->d_rhob, c->stream));
+  }
+  SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
+  SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
+  return SLDG_OK;
+}
+
+// dst <- src advanced by k Strang steps
+int advance(sldg_ctx* c, void* dst, const void* src, int k) {
+  const size_t fb = c->g.N * c->esize;
+  if (dst != src) SLDG_CU(cudaMemcpyAsync(dst, src, fb, cudaMemcpyDeviceToDevice, c->stream));
+  for (int i = 0; i < k; ++i) SLDG_TRY(do_step(c, dst, nullptr));
+  c->bwd_recomputed += k;
+  return SLDG_OK;
+}
+
+// Adjoint of steps [a, b), src holding the state at step a (not modified),
+// with the recomputation slots in `free` (at least one).  As many states as
+// slots allow are stored and consumed in reverse; otherwise the range is
+// split at its midpoint (the state there goes to one slot) and the halves are
+// treated later half first; with a single slot every state is recomputed from
+// src.  Recomputation: none beyond one pass when b - a - 1 <= slots, about
+// log2(b - a) passes when slots run out.
+int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>& free,
+                  const double* cW, void* grad) {
+  const size_t fb = c->g.N * c->esize;
+  const int n = b - a;
+  if (n == 1) return adjoint_step(c, src, a, cW, grad);
+  if ((size_t)(n - 1) <= free.size()) {  // store states a+1 .. b-1, then walk back
+    std::vector<char*> st(free.end() - (n - 1), free.end());
+    free.resize(free.size() - (n - 1));
+    const void* prev = src;
+    for (int i = 0; i < n - 1; ++i) {
+      SLDG_TRY(advance(c, st[i], prev, 1));
+      prev = st[i];
+    }
+    for (int m = b - 1; m > a; --m) SLDG_TRY(adjoint_step(c, st[m - a - 1], m, cW, grad));
+    SLDG_TRY(adjoint_step(c, src, a, cW, grad));
+    free.insert(free.end(), st.begin(), st.end());
+    return SLDG_OK;
+  }
+  if (free.size() == 1) {  // one slot: recompute every state from src
+    char* w = free.back();
+    for (int m = b - 1; m > a; --m) {
+      SLDG_TRY(advance(c, w, src, m - a));
+      SLDG_TRY(adjoint_step(c, w, m, cW, grad));
+    }
+    return adjoint_step(c, src, a, cW, grad);
+  }
+  const int mid = a + n / 2;
+  char* s = free.back();
+  free.pop_back();
+  SLDG_TRY(advance(c, s, src, mid - a));
+  SLDG_TRY(adjoint_range(c, s, mid, b, free, cW, grad));
+  free.push_back(s);
+  (void)fb;
+  return adjoint_range(c, src, a, mid, free, cW, grad);
+}
+
+}  // namespace
+
+extern "C" {
+
 int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
   if (!c || !grad) return SLDG_ERR_BAD_PTR;
   if (!c->recorded) return SLDG_ERR_STATE;
@@ -735,9 +845,6 @@ int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
   const int n = c->rec_nsteps, ck = c->rec_ckpt;
   const size_t fb = g.N * c->esize;
   char* pool = reinterpret_cast<char*>(c->d_ckpool);
-  char* seg = reinterpret_cast<char*>(c->d_seg);
-  void* g2 = c->d_work[0];
-  void* g3 = c->d_work[1];
   // J from the recorded W history (compensated host sum)
   if (J_out) {
     std::vector<double> W(n);
@@ -752,49 +859,34 @@ int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
     }
     *J_out = s + comp;
   }
+  // working memory: g2, g3 and the recomputation slots (as many as a segment
+  // can use, within the free device memory and the slot limit)
+  for (int i = 0; i < 2; ++i)
+    if (!c->d_work[i]) SLDG_TRY(dalloc(&c->d_work[i], fb));
+  SLDG_TRY(ensure_adjoint_scratch(c));
+  const size_t want = (size_t)std::max(1, std::min(ck, n) - 1);
+  size_t slots = want;
+  if (c->slot_limit > 0) slots = std::min(slots, (size_t)c->slot_limit);
+  if (c->seg_count != slots) {
+    dfree(c->d_seg);
+    c->seg_count = 0;
+    size_t freeb = 0, totalb = 0;
+    SLDG_CU(cudaMemGetInfo(&freeb, &totalb));
+    const size_t margin = std::max<size_t>(totalb / 64, (size_t)1 << 30);
+    const size_t fit = freeb > margin ? (freeb - margin) / fb : 0;
+    slots = std::min(slots, fit);
+    if (slots < 1) return SLDG_ERR_OOM;
+    SLDG_TRY(dalloc(&c->d_seg, slots * fb));
+    c->seg_count = slots;
+  }
+  std::vector<char*> free;
+  for (size_t i = 0; i < c->seg_count; ++i) free.push_back(reinterpret_cast<char*>(c->d_seg) + i * fb);
+  c->bwd_recomputed = 0;
   SLDG_CU(cudaMemsetAsync(grad, 0, fb, c->stream));
   const int nseg = (int)c->ck_count;
   for (int sidx = nseg - 1; sidx >= 0; --sidx) {
     const int m0 = sidx * ck, m1 = std::min(m0 + ck, n);
-    SLDG_CU(cudaMemcpyAsync(seg, pool + (size_t)sidx * fb, fb, cudaMemcpyDeviceToDevice, c->stream));
-    for (int m = m0; m < m1 - 1; ++m) {
-      char* cur = seg + (size_t)(m - m0) * fb;
-      SLDG_CU(cudaMemcpyAsync(cur + fb, cur, fb, cudaMemcpyDeviceToDevice, c->stream));
-      SLDG_TRY(do_step(c, cur + fb, nullptr));
-    }
-    for (int m = m1 - 1; m >= m0; --m) {
-      const char* fm = seg + (size_t)(m - m0) * fb;
-      // forward intermediates: g2 = X2 X1 f^m (input of V1), g3 = V1 g2 (input of V2)
-      SLDG_CU(cudaMemcpyAsync(g2, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
-      SLDG_TRY(run_sweep(c, g2, 0, 0.5, false, nullptr, nullptr));
-      SLDG_TRY(run_sweep(c, g2, 1, 0.5, false, nullptr, nullptr));
-      SLDG_TRY(compute_fields(c, g2));
-      SLDG_CU(cudaMemcpyAsync(g3, g2, fb, cudaMemcpyDeviceToDevice, c->stream));
-      SLDG_TRY(run_sweep(c, g3, 2, 1.0, false, nullptr, nullptr));
-      // reverse
-      SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
-      SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
-      SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
-      SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
-      SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1]));
-      SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0]));
-      {
-        KTimer t(c, SLDG_K_OTHER);
-        SLDG_CU(launch_energy_adj(c->d_Eb[0], c->d_Eb[1], c->d_E[0], c->d_E[1], c->d_wx, g.Dx,
-                                  cW ? cW[m] : g.dt, c->stream));
-      }
-      {
-        int nl = 0;
-        KTimer t(c, SLDG_K_POISSON, 4);
-        SLDG_CU(launch_poisson_adj(poisson_args(c), c->d_Eb[0], c->d_Eb[1], c->d_rhob, c->stream, &nl));
-      }
-      {
-        KTimer t(c, SLDG_K_RHO);
-        SLDG_CU(launch_rho_adj(c->prec, grad, g, c->d_wv, c->d_rhob, c->stream));
-      }
-      SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
-      SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
-    }
+    SLDG_TRY(adjoint_range(c, pool + (size_t)sidx * fb, m0, m1, free, cW, grad));
   }
   // the context's field now belongs to the first step; leave f as recorded
   c->have_field = false;

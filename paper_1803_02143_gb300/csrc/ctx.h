@@ -111,9 +111,11 @@ struct sldg_ctx {
   int rec_nsteps = 0, rec_ckpt = 0;
   bool recorded = false;
   double* d_Wrec = nullptr;
-  void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};  // g2, g3, lam, seg...
-  void* d_seg = nullptr;
+  void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};  // g2, g3 of the adjoint step
+  void* d_seg = nullptr;        // recomputation slots, seg_count states of f
   size_t seg_count = 0;
+  int slot_limit = 0;           // upper bound on seg_count (0: as many as fit)
+  long long bwd_recomputed = 0; // Strang steps recomputed by the last backward
   double* d_Eb[2] = {nullptr, nullptr};
   double* d_rhob = nullptr;
   double* d_epart = nullptr;

@@ -170,6 +170,13 @@ class Sldg:
         J = N.sldg_backward(self._ctx, c, grad.data_ptr())
         return J, grad
 
+    def set_slot_limit(self, max_slots: int):
+        N.sldg_set_slot_limit(self._ctx, max_slots)
+
+    def backward_stats(self):
+        """(Strang steps recomputed by the last backward, recomputation slots held)."""
+        return N.sldg_backward_stats(self._ctx)
+
     def initial_param_grad(self, kind: int, params, grad: torch.Tensor) -> float:
         return N.sldg_initial_param_grad(self._ctx, kind, params, grad.data_ptr())
 

@@ -1,5 +1,8 @@
-"""Parity at the benchmark's full size (nonlinear Landau damping, 64^4 cells,
-degree 2, 1.36e9 nodal values) in the launch configuration bench.py times.
+"""Parity at full size, in the launch configuration bench.py times: the
+bench workload (nonlinear Landau damping, 64^4 cells, degree 2, 1.36e9 nodal
+values), the two-stream workload (64^2 x 128^2 cells, degree 2, 5.4e9 values)
+and the large mixed-precision workload (128^4 cells, degree 1, 4.3e9 values,
+FP32 storage).
 
 The oracle cannot step 1.36e9 values, so each stage of the Strang step is
 run alone through the C ABI (the same kernels sldg_step launches) and
@@ -20,9 +23,14 @@ torch = pytest.importorskip("torch")
 NLINES = 48
 
 
+CASES = [("nonlinear_landau_64", "fp64"), ("nonlinear_landau_64", "fp32"),
+         ("two_stream_64x128", "fp64"), ("two_stream_64x128", "fp32"),
+         ("mixed_landau_128", "fp32")]
+
+
 @pytest.fixture(scope="module")
 def big():
-    """One full-size context at a time (FP64, then FP32), built on demand."""
+    """One full-size context at a time, built on demand."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1803_02143_gb300 import build
@@ -34,9 +42,10 @@ def big():
         s.close()
 
 
-def _context(big, orc, prec):
-    if prec in big:
-        return big[prec]
+def _context(big, orc, name, prec):
+    key = (name, prec)
+    if key in big:
+        return big[key]
     for s, _ in list(big.values()):
         s.close()
     big.clear()
@@ -44,13 +53,13 @@ def _context(big, orc, prec):
     from paper_1803_02143_gb300 import configs
 
     torch.cuda.empty_cache()
-    w = configs.workload("nonlinear_landau_64", prec)
+    w = configs.workload(name, prec)
     s = P.Sldg(w.cfg)
     s.set_initial(w.kind, w.params)
     s.step(1)  # a developed state, not the separable initial value
     og = orc.Grid(deg=w.cfg.degree, nc=w.cfg.ncell, lo=w.cfg.lo, hi=w.cfg.hi, dt=w.cfg.dt)
-    big[prec] = (s, og)
-    return big[prec]
+    big[key] = (s, og)
+    return big[key]
 
 
 def _lines(F, d, idx):
@@ -64,10 +73,10 @@ def _lines(F, d, idx):
     return F[:, idx[:, 0], idx[:, 1], idx[:, 2]].T
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,prec", CASES)
 @pytest.mark.parametrize("d", [0, 1, 2, 3])
-def test_fullsize_sweep_sampled_lines(big, orc, prec, d):
-    s, og = _context(big, orc, prec)
+def test_fullsize_sweep_sampled_lines(big, orc, name, prec, d):
+    s, og = _context(big, orc, name, prec)
     F = s.f
     shp = og.shape
     other = [a for a in range(4) if a != 3 - d]  # numpy axes other than d's
@@ -98,9 +107,9 @@ def test_fullsize_sweep_sampled_lines(big, orc, prec, d):
     assert worst < (1e-13 if prec == "fp64" else 2e-6), worst
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fullsize_rho_and_poisson(big, orc, prec):
-    s, og = _context(big, orc, prec)
+@pytest.mark.parametrize("name,prec", CASES)
+def test_fullsize_rho_and_poisson(big, orc, name, prec):
+    s, og = _context(big, orc, name, prec)
     s.compute_fields()
     rho, E1, E2 = s.fields()
     r = rng(77)
