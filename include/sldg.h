@@ -161,6 +161,19 @@ int sldg_set_f(sldg_ctx* ctx, const void* src, int on_device, double t, long lon
  * Errors: ARG (nsteps < 0), CUDA. */
 int sldg_step(sldg_ctx* ctx, int nsteps, double* W_history);
 
+/* One Strang step for each of nbatch states that live in host memory: batch
+ * b is the N elements (context precision) at host_f + b * batch_stride_bytes
+ * (stride 0: the same host state every time); W of its step goes to
+ * W_out[b] (host, nbatch doubles).  Batch b+1 is copied host-to-device on a
+ * second stream, into a library-owned second state buffer, while batch b
+ * is stepped on the context's stream, so the copies and the steps overlap;
+ * host_f should be pinned (page-locked) memory for the copies to run at
+ * full speed and asynchronously.  On return f holds the stepped state of
+ * the last batch and t, step have advanced by one step.  Synchronises.
+ * Errors: BAD_PTR, ARG (nbatch < 1 or a negative stride), OOM, CUDA. */
+int sldg_step_host_batches(sldg_ctx* ctx, const void* host_f, long long batch_stride_bytes,
+                           int nbatch, double* W_out);
+
 /* One 1D sweep in place along direction dim (Sec. 3, Eq. (1d-advection): the
  * one function "executed multiple times with different parameters"):
  *   dim 0, 1: shift a = v_{dim}(node) * dt * frac, periodic in x;

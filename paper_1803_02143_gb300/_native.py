@@ -86,6 +86,7 @@ SIGNATURES = {
     "sldg_get_f": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "sldg_set_f": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_longlong]),
     "sldg_step": (ctypes.c_int, [_VP, ctypes.c_int, _DP]),
+    "sldg_step_host_batches": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_int, _DP]),
     "sldg_sweep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double]),
     "sldg_compute_fields": (ctypes.c_int, [_VP]),
     "sldg_set_field": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
@@ -203,6 +204,12 @@ def sldg_diagnostics(ctx) -> sldg_diag:
 def sldg_sweep_adjoint(ctx, dim: int, frac: float, lam_ptr: int, g_ptr=None, Ebar_ptr=None) -> None:
     _check("sldg_sweep_adjoint", load().sldg_sweep_adjoint(ctx, int(dim), float(frac), _VP(lam_ptr),
                                                            _VP(g_ptr), _VP(Ebar_ptr)))
+
+
+def sldg_step_host_batches(ctx, host_ptr: int, stride_bytes: int, nbatch: int, W_out) -> None:
+    _check("sldg_step_host_batches",
+           load().sldg_step_host_batches(ctx, _VP(host_ptr), int(stride_bytes), int(nbatch),
+                                         _dptr(W_out)))
 
 
 def sldg_record(ctx, nsteps: int, ckpt_every: int, W_history=None) -> None:

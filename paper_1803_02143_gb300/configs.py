@@ -42,6 +42,12 @@ WORKLOADS = {
     # profiling captures
     "nonlinear_landau_48": Workload("nonlinear_landau_48", _landau(2, 48, 0.05, 0.5),
                                     N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 400),
+    # the 64^4 workload's x-grid with 32^2 v-cells (3.4e8 dofs, 2.7 GB FP64): same x1
+    # and x2 lines as the bench workload, for profiling captures
+    "nonlinear_landau_64x32": Workload(
+        "nonlinear_landau_64x32",
+        Config(degree=2, ncell=(64, 64, 32, 32), lo=LANDAU_LO, hi=LANDAU_HI, dt=0.05),
+        N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 400),
     # two-stream instability, 64^2 x 128^2 cells, degree 2 (5.4e9 dofs), dt 0.05 to T = 40
     "two_stream_64x128": Workload(
         "two_stream_64x128",

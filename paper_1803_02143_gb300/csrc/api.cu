@@ -178,6 +178,17 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_W); dfree(c->d_diag); dfree(c->d_Wrec); dfree(c->d_rhob); dfree(c->d_epart);
   dfree(c->d_ckpool); dfree(c->d_seg);
   for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
+  dfree(c->d_alt);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_up[i]) cudaEventDestroy(c->ev_up[i]);
+    if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+    c->ev_up[i] = c->ev_free[i] = nullptr;
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
+  if (c->h_W) cudaFreeHost(c->h_W);
+  c->h_W = nullptr;
+  c->h_W_cap = 0;
   for (auto& e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
 }
@@ -601,6 +612,67 @@ int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
                             c->stream));
     SLDG_CU(cudaStreamSynchronize(c->stream));
   }
+  return SLDG_OK;
+}
+
+// Host batches: batch b+1 is uploaded on a copy stream into the buffer that
+// batch b-1 used while batch b is stepped on the context's stream; W of each
+// batch goes to pinned host memory as soon as its step ends.
+int sldg_step_host_batches(sldg_ctx* c, const void* host_f, long long batch_stride_bytes,
+                           int nbatch, double* W_out) {
+  if (!c || !host_f || !W_out) return SLDG_ERR_BAD_PTR;
+  if (nbatch < 1 || batch_stride_bytes < 0) return SLDG_ERR_ARG;
+  const size_t fb = c->g.N * c->esize;
+  if (!c->d_alt) SLDG_TRY(dalloc(&c->d_alt, fb));
+  if (!c->copy_stream) SLDG_CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    if (!c->ev_up[i]) SLDG_CU(cudaEventCreateWithFlags(&c->ev_up[i], cudaEventDisableTiming));
+    if (!c->ev_free[i]) SLDG_CU(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
+  }
+  if (c->h_W_cap < nbatch) {
+    if (c->h_W) cudaFreeHost(c->h_W);
+    c->h_W = nullptr;
+    c->h_W_cap = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_W), (size_t)nbatch * sizeof(double),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_W = nullptr;
+      return SLDG_ERR_OOM;
+    }
+    c->h_W_cap = nbatch;
+  }
+  SLDG_TRY(ensure_W(c, nbatch));
+  void* buf[2] = {c->f, c->d_alt};
+  const char* src = static_cast<const char*>(host_f);
+  // the copy stream may overwrite a buffer only after earlier work on it
+  SLDG_CU(cudaEventRecord(c->ev_free[0], c->stream));
+  SLDG_CU(cudaEventRecord(c->ev_free[1], c->stream));
+  SLDG_CU(cudaStreamWaitEvent(c->copy_stream, c->ev_free[0], 0));
+  SLDG_CU(cudaMemcpyAsync(buf[0], src, fb, cudaMemcpyHostToDevice, c->copy_stream));
+  SLDG_CU(cudaEventRecord(c->ev_up[0], c->copy_stream));
+  for (int b = 0; b < nbatch; ++b) {
+    const int k = b & 1;
+    if (b + 1 < nbatch) {
+      const int k1 = k ^ 1;
+      SLDG_CU(cudaStreamWaitEvent(c->copy_stream, c->ev_free[k1], 0));
+      SLDG_CU(cudaMemcpyAsync(buf[k1], src + (size_t)(b + 1) * batch_stride_bytes, fb,
+                              cudaMemcpyHostToDevice, c->copy_stream));
+      SLDG_CU(cudaEventRecord(c->ev_up[k1], c->copy_stream));
+    }
+    SLDG_CU(cudaStreamWaitEvent(c->stream, c->ev_up[k], 0));
+    c->have_field = false;
+    invalidate_vmats(c);
+    SLDG_TRY(do_step(c, buf[k], c->d_W + b));
+    SLDG_CU(cudaEventRecord(c->ev_free[k], c->stream));
+    SLDG_CU(cudaMemcpyAsync(c->h_W + b, c->d_W + b, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+  }
+  if ((nbatch - 1) & 1)  // the last state sits in the second buffer
+    SLDG_CU(cudaMemcpyAsync(c->f, c->d_alt, fb, cudaMemcpyDeviceToDevice, c->stream));
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  std::memcpy(W_out, c->h_W, (size_t)nbatch * sizeof(double));
+  c->t += c->g.dt;
+  c->step += 1;
   return SLDG_OK;
 }
 

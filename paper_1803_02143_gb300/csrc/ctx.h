@@ -124,6 +124,15 @@ struct sldg_ctx {
   double rec_t0 = 0.0;
   long long rec_step0 = 0;
 
+  // host-batch pipeline (sldg_step_host_batches): a second state buffer, a
+  // copy stream, and pinned host slots for the per-batch W
+  void* d_alt = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_up[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  double* h_W = nullptr;
+  int h_W_cap = 0;
+
   // state
   double t = 0.0;
   long long step = 0;

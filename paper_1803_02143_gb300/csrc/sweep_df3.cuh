@@ -72,33 +72,39 @@ __device__ __forceinline__ void df3_load_cell(const double* __restrict__ raw, in
   }
 }
 
-// One output cell for both lanes: y = A xa + B xb, stored as double2 rows
-// out[j * rstride].  An empty asm with a memory clobber before each output row
-// keeps its matrix reads next to their use (loading all 2N^2 float4 entries
-// of a cell up front would spill).
+// y = A xa + B xb for one cell of both lanes: the 2N source terms in order
+// (A columns, then B columns), each applied to all N outputs, so the N
+// double-float accumulations are independent chains.  An empty asm with a
+// memory clobber per term keeps that term's matrix reads next to their use
+// (loading all 2N^2 float4 entries of a cell up front would spill).
+template <int N>
+__device__ __forceinline__ void df3_accumulate(const float4* __restrict__ M, const float2* ah,
+                                               const float2* al, const float2* bh,
+                                               const float2* bl, float2* sh, float2* sl) {
+#pragma unroll
+  for (int t = 0; t < 2 * N; ++t) {
+    asm volatile("" ::: "memory");
+    const float2 xh = t < N ? ah[t] : bh[t - N];
+    const float2 xl = t < N ? al[t] : bl[t - N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const float4 m = M[t < N ? j * N + t : N * N + j * N + (t - N)];
+      if (t == 0) df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), xh, xl, sh[j], sl[j]);
+      else df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), xh, xl, sh[j], sl[j]);
+    }
+  }
+}
+
 template <int N, bool OUT_DF>
 __device__ __forceinline__ void df3_cell(const float4* __restrict__ M, const float2* ah,
                                          const float2* al, const float2* bh, const float2* bl,
                                          double* out, long long rstride) {
+  float2 sh[N], sl[N];
+  df3_accumulate<N>(M, ah, al, bh, bl, sh, sl);
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    asm volatile("" ::: "memory");
-    float2 sh, sl;
-    float4 m = M[j * N];
-    df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[0], al[0], sh, sl);
-#pragma unroll
-    for (int l = 1; l < N; ++l) {
-      m = M[j * N + l];
-      df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[l], al[l], sh, sl);
-    }
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      m = M[N * N + j * N + l];
-      df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), bh[l], bl[l], sh, sl);
-    }
+  for (int j = 0; j < N; ++j)
     *reinterpret_cast<double2*>(out + j * rstride) =
-        make_double2(store_pair<OUT_DF>(sh.x, sl.x), store_pair<OUT_DF>(sh.y, sl.y));
-  }
+        make_double2(store_pair<OUT_DF>(sh[j].x, sl[j].x), store_pair<OUT_DF>(sh[j].y, sl[j].y));
 }
 
 // Outputs cb .. ce-1 of one column pair: a sliding window over the source
@@ -303,10 +309,8 @@ __global__ void __launch_bounds__(kX1Df3Threads, 3)
   float4* smat = reinterpret_cast<float4*>(smraw);
   const int D = nc * N;
   const int TL = R * D;  // doubles per tile
-  double* rawb[2];
-  rawb[0] = reinterpret_cast<double*>(smraw + MN * sizeof(float4));
-  rawb[1] = rawb[0] + TL;
-  float2* ph = reinterpret_cast<float2*>(rawb[1] + TL);
+  double* raw0 = reinterpret_cast<double*>(smraw + MN * sizeof(float4));  // two tile buffers
+  float2* ph = reinterpret_cast<float2*>(raw0 + 2 * TL);
   float2* pl = ph + TL / 2;
   const int TPP = 1 << tpp_log2;  // threads per line pair
   const int p = threadIdx.x >> tpp_log2, t = threadIdx.x & (TPP - 1);
@@ -321,10 +325,10 @@ __global__ void __launch_bounds__(kX1Df3Threads, 3)
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  issue(tile0, rawb[0]);
+  issue(tile0, raw0);
   int b = 0;
   for (long long tile = tile0; tile < tile1; ++tile, b ^= 1) {
-    double* cur = rawb[b];
+    double* cur = raw0 + b * TL;
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     const int key = (int)(((tile * R) / key_div) % key_mod);
     for (int i = threadIdx.x; i < MN; i += blockDim.x) {
@@ -344,7 +348,7 @@ __global__ void __launch_bounds__(kX1Df3Threads, 3)
       }
     }
     __syncthreads();
-    if (tile + 1 < tile1) issue(tile + 1, rawb[b ^ 1]);
+    if (tile + 1 < tile1) issue(tile + 1, raw0 + (b ^ 1) * TL);
     if (cb < ce) {
       const float2* rh = ph + p * D;
       const float2* rl = pl + p * D;
@@ -365,24 +369,14 @@ __global__ void __launch_bounds__(kX1Df3Threads, 3)
           bh[l] = rh[kb * N + l];
           bl[l] = rl[kb * N + l];
         }
+        {
+          float2 sh[N], sl[N];
+          df3_accumulate<N>(smat, ah, al, bh, bl, sh, sl);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          asm volatile("" ::: "memory");
-          float2 sh, sl;
-          float4 m = smat[j * N];
-          df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[0], al[0], sh, sl);
-#pragma unroll
-          for (int l = 1; l < N; ++l) {
-            m = smat[j * N + l];
-            df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), ah[l], al[l], sh, sl);
+          for (int j = 0; j < N; ++j) {
+            oa[c * N + j] = store_pair<OUT_DF>(sh[j].x, sl[j].x);
+            oa[D + c * N + j] = store_pair<OUT_DF>(sh[j].y, sl[j].y);
           }
-#pragma unroll
-          for (int l = 0; l < N; ++l) {
-            m = smat[N * N + j * N + l];
-            df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), bh[l], bl[l], sh, sl);
-          }
-          oa[c * N + j] = store_pair<OUT_DF>(sh.x, sl.x);
-          oa[D + c * N + j] = store_pair<OUT_DF>(sh.y, sl.y);
         }
 #pragma unroll
         for (int l = 0; l < N; ++l) {

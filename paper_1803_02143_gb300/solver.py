@@ -125,6 +125,22 @@ class Sldg:
         N.sldg_step(self._ctx, nsteps, W)
         return W[:nsteps] if history else None
 
+    def step_host_batches(self, host: torch.Tensor, nbatch: int | None = None):
+        """One Strang step for each state in ``host`` (a CPU tensor, pinned
+        for overlapped copies): shape ``(nbatch,) + Config.shape`` or
+        ``Config.shape`` with ``nbatch`` repeats of the same state.  Returns
+        W of each batch's step; ``f`` ends as the last batch's stepped state."""
+        assert not host.is_cuda and host.dtype == self.cfg.dtype and host.is_contiguous()
+        if nbatch is None:
+            assert host.numel() % self.cfg.numel == 0
+            nbatch, stride = host.numel() // self.cfg.numel, self.cfg.numel * host.element_size()
+        else:
+            assert host.numel() == self.cfg.numel
+            stride = 0
+        W = np.zeros(nbatch)
+        N.sldg_step_host_batches(self._ctx, host.data_ptr(), stride, nbatch, W)
+        return W
+
     def sweep(self, dim: int, frac: float):
         N.sldg_sweep(self._ctx, dim, frac)
 

@@ -289,3 +289,26 @@ def test_launch_count_and_timing(lib, orc):
     for k in ("x1", "x2", "v1", "v2"):
         assert t[k][1] >= 2 * (2 if k in ("x1", "x2") else 1) and t[k][0] > 0
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_host_batches_match_single_steps(lib, orc, prec):
+    # three host states stepped with overlapped uploads give the bits of
+    # one sldg_step each (the same kernels on the second buffer)
+    s, og = make(lib, orc, 2, (7, 6, 8, 9), dt=0.1, prec=prec)
+    host = torch.empty((3,) + s.cfg.shape, dtype=s.cfg.dtype, pin_memory=True)
+    for b, eps in enumerate((0.5, 0.1, 0.3)):
+        s.set_initial(0, (eps, 0.5, 0.5))
+        s.get_f(host[b])
+    torch.cuda.synchronize()
+    W = s.step_host_batches(host)
+    last = s.f.clone()
+    for b in range(3):
+        s.set_f(host[b].cuda())
+        Wb = s.step(1, history=True)
+        assert W[b] == Wb[0]
+    assert torch.equal(s.f, last)
+    # stride 0: the same state every time
+    W0 = s.step_host_batches(host[1].contiguous(), 4)
+    assert np.all(W0 == W[1])
+    s.close()
