@@ -323,6 +323,8 @@ template <int N, bool IN_DF, bool OUT_DF>
 cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st);
 template <int N, bool IN_DF, bool OUT_DF>
 cudaError_t launch_x1_df3_T(const SweepArgs& a, cudaStream_t st);
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st);
 
 // Launch the packed kernels when they apply (forward, degree <= 2, aligned
 // layout, even x1 tile height); returns cudaErrorNotSupported otherwise.
@@ -334,7 +336,9 @@ cudaError_t launch_sweep_df2_T(const SweepArgs& a, cudaStream_t st) {
   if (a.adjoint || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
   if (a.dim == 0) {
     {
-      const cudaError_t e3 = launch_x1_df3_T<N, IN_DF, OUT_DF>(a, st);
+      cudaError_t e3 = launch_x1_warp_T<N, IN_DF, OUT_DF>(a, st);
+      if (e3 != cudaErrorNotSupported) return e3;
+      e3 = launch_x1_df3_T<N, IN_DF, OUT_DF>(a, st);
       if (e3 != cudaErrorNotSupported) return e3;
     }
     const int R = a.lines_per_tile;

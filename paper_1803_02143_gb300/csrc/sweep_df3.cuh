@@ -419,4 +419,147 @@ cudaError_t launch_x1_df3_T(const SweepArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// x1 forward sweep, FP64 storage, packed double-float, warp per line pair.
+// Lines 2p and 2p+1 (one v1 node whenever D1 is even) are the two lanes.
+// Every warp owns a run of line pairs and three private shared buffers of
+// 2 D doubles: two raw buffers (the next pair is loaded by cp.async while
+// the current one is computed) and one plane buffer of (hA, hB, lA, lB)
+// float4 per position.  Per pair: wait for its raw data | convert to planes
+// | outputs of the pair into the consumed raw buffer | copy it out.  Only
+// warp-level synchronisation: warps never wait for each other.
+// ---------------------------------------------------------------------------
+constexpr int kX1WarpPairs = 8;  // line pairs per warp
+
+template <int N>
+__device__ __forceinline__ void x1w_load_cell(const float4* __restrict__ pl, int k,
+                                              float2* xh, float2* xl) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float4 u = pl[k * N + l];
+    xh[l] = make_float2(u.x, u.y);
+    xl[l] = make_float2(u.z, u.w);
+  }
+}
+
+template <int N, bool IN_DF, bool OUT_DF>
+__global__ void __launch_bounds__(256, 3)
+    k_sweep_x1_warp(double* __restrict__ f, int nc, long long npairs, int pairs_per_warp,
+                    const float2* __restrict__ ab2, const int* __restrict__ svec, long long mcount,
+                    int key_div, int key_mod) {
+  constexpr int MN = 2 * N * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int D = nc * N;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  // per warp: matrices, then raw0 | raw1 | planes (2 D doubles each)
+  const size_t wbytes = MN * sizeof(float4) + 3 * (size_t)(2 * D) * sizeof(double);
+  unsigned char* wb = smraw + wib * wbytes;
+  float4* smat = reinterpret_cast<float4*>(wb);
+  double* raw0 = reinterpret_cast<double*>(wb + MN * sizeof(float4));
+  float4* pl = reinterpret_cast<float4*>(raw0 + 4 * D);
+  const long long gw = (long long)blockIdx.x * nwarps + wib;
+  const long long p0 = gw * pairs_per_warp;
+  const long long p1 = min(p0 + pairs_per_warp, npairs);
+  const int cpl = (nc + 31) >> 5;  // cells per lane
+  const int cb = min(lane * cpl, nc), ce = min(cb + cpl, nc);
+
+  auto issue = [&](long long pair, double* dst) {
+    const double* src = f + pair * 2 * D;
+    for (int i = lane; i < D; i += 32) cp_async16(dst + 2 * i, src + 2 * i);  // 2 D doubles
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (p0 < p1) issue(p0, raw0);
+  int key_cur = -1, sa = 0;
+  int bsel = 0;
+  for (long long pair = p0; pair < p1; ++pair, bsel ^= 1) {
+    double* cur = raw0 + bsel * 2 * D;
+    if (pair + 1 < p1) {
+      issue(pair + 1, raw0 + (bsel ^ 1) * 2 * D);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    const int key = (int)(((pair * 2) / key_div) % key_mod);
+    if (key != key_cur) {  // warp-uniform
+      if (lane < MN) {
+        const float2 a = ab2[(long long)lane * mcount + key];
+        smat[lane] = make_float4(a.x, a.x, a.y, a.y);
+      }
+      if (MN > 32)
+        for (int i = lane + 32; i < MN; i += 32) {
+          const float2 a = ab2[(long long)i * mcount + key];
+          smat[i] = make_float4(a.x, a.x, a.y, a.y);
+        }
+      sa = wrap_cell(-svec[key] - 1, nc);
+      key_cur = key;
+    }
+    __syncwarp();
+    for (int k = lane; k < D; k += 32) {  // planes: (hA, hB, lA, lB) per position
+      float h0, l0, h1, l1;
+      load_pair<IN_DF>(cur[k], h0, l0);
+      load_pair<IN_DF>(cur[D + k], h1, l1);
+      pl[k] = make_float4(h0, h1, l0, l1);
+    }
+    __syncwarp();
+    if (cb < ce) {
+      int ka = cb + sa;
+      if (ka >= nc) ka -= nc;
+      float2 ah[N], al[N], bh[N], bl[N];
+      x1w_load_cell<N>(pl, ka, ah, al);
+#pragma unroll 1
+      for (int c = cb; c < ce; ++c) {
+        const int kb = ka + 1 == nc ? 0 : ka + 1;
+        x1w_load_cell<N>(pl, kb, bh, bl);
+        float2 sh[N], sl[N];
+        df3_accumulate<N>(smat, ah, al, bh, bl, sh, sl);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          cur[c * N + j] = store_pair<OUT_DF>(sh[j].x, sl[j].x);
+          cur[D + c * N + j] = store_pair<OUT_DF>(sh[j].y, sl[j].y);
+        }
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          ah[l] = bh[l];
+          al[l] = bl[l];
+        }
+        ka = kb;
+      }
+    }
+    __syncwarp();
+    double2* dst = reinterpret_cast<double2*>(f + pair * 2 * D);
+    const double2* src = reinterpret_cast<const double2*>(cur);
+    for (int i = lane; i < D; i += 32) dst[i] = src[i];
+    __syncwarp();
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st) {
+  double* f = reinterpret_cast<double*>(a.f);
+  const long long D = (long long)a.nc * N;
+  const long long lines = a.outer;
+  if ((D & 1) || (lines & 1) || (a.key_div & 1) || a.key_div > 0x7fffffffLL ||
+      a.key_mod > 0x7fffffffLL)
+    return cudaErrorNotSupported;
+  const size_t wbytes = (size_t)(2 * N * N) * sizeof(float4) + 3 * (size_t)(2 * D) * sizeof(double);
+  // three CTAs per SM share 228 KB, less 1 KB reserved per CTA
+  int nwarps = 8;
+  while (nwarps > 1 && nwarps * wbytes > 76800) nwarps /= 2;
+  if (nwarps * wbytes > 200 * 1024) return cudaErrorNotSupported;
+  const long long npairs = lines / 2;
+  const long long warps = (npairs + kX1WarpPairs - 1) / kX1WarpPairs;
+  const long long blocks = (warps + nwarps - 1) / nwarps;
+  if (blocks > 0x7fffffffLL) return cudaErrorNotSupported;
+  const size_t smem = nwarps * wbytes;
+  auto kfn = k_sweep_x1_warp<N, IN_DF, OUT_DF>;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  kfn<<<(unsigned)blocks, nwarps * 32, smem, st>>>(f, a.nc, npairs, kX1WarpPairs,
+                                                  reinterpret_cast<const float2*>(a.ab2), a.s,
+                                                  a.mcount, (int)a.key_div, (int)a.key_mod);
+  return cudaGetLastError();
+}
+
 }  // namespace sldg
