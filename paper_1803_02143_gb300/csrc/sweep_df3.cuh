@@ -20,7 +20,8 @@ namespace sldg {
 constexpr int kDf3Threads = 256;
 constexpr int kDf3Pairs = kStridedW / 2;             // 16 column pairs
 constexpr int kDf3Groups = kDf3Threads / kDf3Pairs;  // 16 cell runs
-constexpr int kDf3TilesPerCta = 4;                   // outer indices walked by one CTA
+constexpr int kDf3TilesPerCtaV = 8;  // outer indices walked by one CTA: v-sweeps
+constexpr int kDf3TilesPerCtaX = 8;  // x2 sweep
 
 // float4 entries per lane pair: odd, so the 16 pairs' matrix reads of a
 // quarter warp fall in distinct banks
@@ -29,10 +30,11 @@ __host__ __device__ constexpr int df3_mat_stride() {
   return 2 * N * N + 1;
 }
 
+// matrices, then nbuf tile buffers of D + N rows (N zero rows each)
 template <int N, bool PERCOL>
-inline size_t strided_df3_smem(long long D) {
+inline size_t strided_df3_smem(long long D, int nbuf) {
   const size_t mats = PERCOL ? (size_t)kDf3Pairs * df3_mat_stride<N>() : (size_t)(2 * N * N);
-  return mats * sizeof(float4) + (size_t)(D + N) * kStridedW * sizeof(double);
+  return mats * sizeof(float4) + nbuf * (size_t)(D + N) * kStridedW * sizeof(double);
 }
 
 // Tile conversion in place: each 16-byte column pair of a staged row,
@@ -152,12 +154,13 @@ __device__ __forceinline__ void df3_run(const double* __restrict__ raw, const fl
 // x-node), periodic or zero inflow; consecutive outer indices of a CTA share
 // its matrices.  Else (x2-sweep, periodic): one matrix per tile, key =
 // (o / key_div) % key_mod.
-// Three CTAs per SM: at most 80 registers per thread, and 54 KB of shared
-// memory per CTA for 192-node lines.
+// With two tile buffers (nbuf = 2) the next tile is loaded (cp.async) while
+// the current one is computed; two CTAs per SM (105 KB of shared memory per
+// CTA for 192-node lines).  Longer lines use one buffer.
 template <int N, bool PERIODIC, bool PERCOL, bool IN_DF, bool OUT_DF>
-__global__ void __launch_bounds__(kDf3Threads, 3)
+__global__ void __launch_bounds__(kDf3Threads, 2)
     k_sweep_strided_df3(double* __restrict__ f, int ncols, long long rstride, long long ostride,
-                        int nc, int outer, const float2* __restrict__ ab2,
+                        int nc, int outer, int nbuf, const float2* __restrict__ ab2,
                         const int* __restrict__ svec, long long mcount, int key_div, int key_mod) {
   static_assert(PERCOL || PERIODIC, "the per-tile matrix form serves the periodic x2 sweep");
   constexpr int W = kStridedW;
@@ -192,35 +195,67 @@ __global__ void __launch_bounds__(kDf3Threads, 3)
       sa1 = wrap_cell(sa1, nc);
     }
   }
-  if (!PERIODIC)  // the zero cell, rows D .. D+N-1 (never written by tile loads)
-    for (int i = threadIdx.x; i < N * W; i += blockDim.x) raw[D * W + i] = 0.0;
+  const int bstride = (D + N) * W;  // doubles per tile buffer
+  if (!PERIODIC)  // the zero cell, rows D .. D+N-1 of each buffer (never loaded)
+    for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
+      raw[D * W + i] = 0.0;
+      if (nbuf == 2) raw[bstride + D * W + i] = 0.0;
+    }
   const float4* M = PERCOL ? smat + q * MS : smat;
   const int chunks = D * (W / 2);  // 16-byte chunks of a full tile
   const int vchunks = nvalid / 2;  // valid chunks per row
 
-  for (int o = blockIdx.y; o < outer; o += gridDim.y) {
-    double* fb = f + (long long)o * ostride + col0;
-    if (!PERCOL) {
-      const int key = (o / key_div) % key_mod;
-      for (int i = threadIdx.x; i < MN; i += blockDim.x) {
-        const float2 a = ab2[(long long)i * mcount + key];
-        smat[i] = make_float4(a.x, a.x, a.y, a.y);
-      }
-      sa0 = wrap_cell(-svec[key] - 1, nc);
-      sa1 = sa0;
-    }
+  auto issue = [&](int o, double* dst) {
+    const double* src = f + (long long)o * ostride + col0;
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
       const int r = i / (W / 2), cq = i - r * (W / 2);
-      if (cq < vchunks) cp_async16(raw + r * W + 2 * cq, fb + r * rstride + 2 * cq);
+      if (cq < vchunks) cp_async16(dst + r * W + 2 * cq, src + r * rstride + 2 * cq);
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  // outer indices of this CTA: o0, o0 + ostep, ... below o1.  v-sweeps stride
+  // by the grid (their matrices are per column); the x2 sweep takes a
+  // contiguous run so that its per-tile matrix (one v2 node per D2
+  // consecutive planes) is restaged only when the node changes.
+  int o0, o1, ostep;
+  if (PERCOL) {
+    o0 = blockIdx.y;
+    o1 = outer;
+    ostep = gridDim.y;
+  } else {
+    const int per = (outer + gridDim.y - 1) / gridDim.y;
+    o0 = blockIdx.y * per;
+    o1 = min(outer, o0 + per);
+    ostep = 1;
+  }
+  int key_cur = -1;
+  if (nbuf == 2 && o0 < o1) issue(o0, raw);
+  int b = 0;
+  for (int o = o0; o < o1; o += ostep, b ^= 1) {
+    double* fb = f + (long long)o * ostride + col0;
+    double* cur = raw + (nbuf == 2 ? b : 0) * bstride;
+    if (nbuf == 1) issue(o, cur);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (!PERCOL) {
+      const int key = (o / key_div) % key_mod;
+      if (key != key_cur) {  // uniform over the CTA
+        for (int i = threadIdx.x; i < MN; i += blockDim.x) {
+          const float2 a = ab2[(long long)i * mcount + key];
+          smat[i] = make_float4(a.x, a.x, a.y, a.y);
+        }
+        sa0 = wrap_cell(-svec[key] - 1, nc);
+        sa1 = sa0;
+        key_cur = key;
+      }
+    }
     __syncthreads();
-    df3_pair_planar<IN_DF>(raw, D * (W / 2));
+    df3_pair_planar<IN_DF>(cur, D * (W / 2));
     __syncthreads();
+    if (nbuf == 2 && o + ostep < o1) issue(o + ostep, raw + (b ^ 1) * bstride);
 
     if (active) {
-      if (sa0 == sa1) df3_run<N, PERIODIC, true, OUT_DF>(raw, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
-      else df3_run<N, PERIODIC, false, OUT_DF>(raw, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
+      if (sa0 == sa1) df3_run<N, PERIODIC, true, OUT_DF>(cur, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
+      else df3_run<N, PERIODIC, false, OUT_DF>(cur, M, c0, cb, ce, sa0, sa1, nc, fb, rstride);
     }
     __syncthreads();  // the tile (and a per-tile matrix) is rewritten next
   }
@@ -255,25 +290,30 @@ cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st) {
       a.key_mod > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
     return cudaErrorNotSupported;
   const long long ncolblk = (ncols + kStridedW - 1) / kStridedW;
-  long long gy = (outer + kDf3TilesPerCta - 1) / kDf3TilesPerCta;
+  const int tpc = percol ? kDf3TilesPerCtaV : kDf3TilesPerCtaX;
+  long long gy = (outer + tpc - 1) / tpc;
   if (gy > 65535) gy = 65535;
   const dim3 grid((unsigned)ncolblk, (unsigned)gy);
   using KFn = decltype(&k_sweep_strided_df3<N, true, true, IN_DF, OUT_DF>);
   KFn kfn;
-  size_t smem;
-  if (!percol) {
-    kfn = k_sweep_strided_df3<N, true, false, IN_DF, OUT_DF>;
-    smem = strided_df3_smem<N, false>(D);
-  } else {
-    kfn = a.periodic ? k_sweep_strided_df3<N, true, true, IN_DF, OUT_DF>
-                     : k_sweep_strided_df3<N, false, true, IN_DF, OUT_DF>;
-    smem = strided_df3_smem<N, true>(D);
+  if (!percol) kfn = k_sweep_strided_df3<N, true, false, IN_DF, OUT_DF>;
+  else kfn = a.periodic ? k_sweep_strided_df3<N, true, true, IN_DF, OUT_DF>
+                        : k_sweep_strided_df3<N, false, true, IN_DF, OUT_DF>;
+  // two buffers while two CTAs still fit on an SM (228 KB, 1 KB reserved each)
+  int nbuf = 2;
+  auto smem_of = [&](int nb) {
+    return percol ? strided_df3_smem<N, true>(D, nb) : strided_df3_smem<N, false>(D, nb);
+  };
+  size_t smem = smem_of(nbuf);
+  if (nbuf == 2 && smem > 115 * 1024) {
+    nbuf = 1;
+    smem = smem_of(1);
   }
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
-  kfn<<<grid, kDf3Threads, smem, st>>>(f, (int)ncols, rstride, ostride, a.nc, (int)outer, ab2, a.s,
-                                       a.mcount, (int)a.key_div, (int)a.key_mod);
+  kfn<<<grid, kDf3Threads, smem, st>>>(f, (int)ncols, rstride, ostride, a.nc, (int)outer, nbuf, ab2,
+                                       a.s, a.mcount, (int)a.key_div, (int)a.key_mod);
   return cudaGetLastError();
 }
 
