@@ -63,6 +63,9 @@ extern "C" {
                                    default double-float arithmetic on the FP32
                                    pipe (same results to ~1e-15; slower on GB300,
                                    whose FP64 pipe is about 1/64 of FP32) */
+#define SLDG_FLAG_NO_XFUSION 2  /* FP32 storage: run the X1 and X2 half drifts
+                                   as two sweeps instead of one fused pass over
+                                   each x-plane (same results, bit for bit) */
 
 #define SLDG_VBC_ZERO_INFLOW 0 /* v-sweeps drop source cells outside the box */
 #define SLDG_VBC_PERIODIC 1    /* v-sweeps wrap (test mode: exact mass) */
@@ -82,7 +85,8 @@ extern "C" {
 #define SLDG_K_OTHER 7
 #define SLDG_K_ADJ_X 8
 #define SLDG_K_ADJ_V 9
-#define SLDG_NUM_KINDS 10
+#define SLDG_K_X12 10 /* fused X1, X2 half drifts (FP32 storage) */
+#define SLDG_NUM_KINDS 11
 
 typedef struct {
   int degree;       /* l in 0..3 (dG(l+1)); l+1 nodes per cell and direction */
@@ -94,7 +98,7 @@ typedef struct {
   int vbc;          /* SLDG_VBC_ZERO_INFLOW or SLDG_VBC_PERIODIC */
   int poisson_kmax; /* Fourier modes |m_d| <= K_d; < 0 selects
                        K_d = min(ncell_d - 1, (D_d - 1) / 2) */
-  int flags;        /* 0 or SLDG_FLAG_NATIVE_FP64 */
+  int flags;        /* 0 or SLDG_FLAG_* bits */
 } sldg_config;
 
 typedef struct {

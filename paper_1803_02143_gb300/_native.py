@@ -26,13 +26,14 @@ SLDG_ERR_ARG = -8
 SLDG_FP64 = 0
 SLDG_FP32 = 1
 SLDG_FLAG_NATIVE_FP64 = 1
+SLDG_FLAG_NO_XFUSION = 2
 SLDG_VBC_ZERO_INFLOW = 0
 SLDG_VBC_PERIODIC = 1
 SLDG_INIT_LANDAU = 0
 SLDG_INIT_TWO_STREAM = 1
 SLDG_INIT_TWO_STREAM_PAPER = 2
 
-KIND_NAMES = ("x1", "x2", "v1", "v2", "rho", "poisson", "vmat", "other", "adj_x", "adj_v")
+KIND_NAMES = ("x1", "x2", "v1", "v2", "rho", "poisson", "vmat", "other", "adj_x", "adj_v", "x12")
 SLDG_NUM_KINDS = len(KIND_NAMES)
 
 

@@ -145,7 +145,7 @@ int validate(const sldg_config* cfg) {
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
   if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
   if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->flags & ~SLDG_FLAG_NATIVE_FP64) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION)) return SLDG_ERR_BAD_CONFIG;
   return SLDG_OK;
 }
 
@@ -357,10 +357,36 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // after the step; the five intermediate sub-step states in between are kept
 // as double-float (hi, lo) pairs in the same 8-byte elements, so the
 // conversion to and from the FP32 pipe's format happens once per step.
+// X1(tau/2) X2(tau/2) as one fused pass (FP32 storage); false when the
+// layout does not suit it and the two sweeps must run separately
+int run_x12(sldg_ctx* c, void* buf, bool* done) {
+  *done = false;
+  if (c->prec != SLDG_FP32 || (c->cfg.flags & SLDG_FLAG_NO_XFUSION)) return SLDG_OK;
+  SLDG_TRY(ensure_xmats(c, 0, 0.5));
+  SLDG_TRY(ensure_xmats(c, 1, 0.5));
+  KTimer t(c, SLDG_K_X12);
+  const cudaError_t e = launch_sweep_x12_f32(buf, c->g, c->xm[0].ab, c->xm[0].s, c->xm[1].ab,
+                                             c->xm[1].s, c->stream);
+  if (e == cudaErrorNotSupported) {
+    t.n = 0;  // nothing launched
+    return SLDG_OK;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SLDG_ERR_CUDA;
+  }
+  *done = true;
+  return SLDG_OK;
+}
+
 int do_step(sldg_ctx* c, void* buf, double* Wslot) {
   const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
-  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
-  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
+  bool fused = false;
+  SLDG_TRY(run_x12(c, buf, &fused));
+  if (!fused) {
+    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
+    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
+  }
   SLDG_TRY(compute_fields(c, buf, df));
   if (Wslot) {
     KTimer t(c, SLDG_K_OTHER);
@@ -368,8 +394,11 @@ int do_step(sldg_ctx* c, void* buf, double* Wslot) {
   }
   SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
   SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
+  SLDG_TRY(run_x12(c, buf, &fused));
+  if (!fused) {
+    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
+    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
+  }
   return SLDG_OK;
 }
 
@@ -457,7 +486,7 @@ int build_tables(sldg_ctx* c) {
   SLDG_CU(cudaMemcpy(c->d_F2, F2.data(), F2.size() * sizeof(double2), cudaMemcpyHostToDevice));
   SLDG_CU(cudaMemcpy(c->d_G2, G2.data(), G2.size() * sizeof(double2), cudaMemcpyHostToDevice));
   SLDG_TRY(dalloc(&c->d_T, (size_t)D1 * M1 * sizeof(double2)));
-  SLDG_TRY(dalloc(&c->d_R, (size_t)M2 * M1 * sizeof(double2)));
+  SLDG_TRY(dalloc(&c->d_R, 2 * (size_t)M2 * M1 * sizeof(double2)));  // c_1 rho_hat, c_2 rho_hat
   SLDG_TRY(dalloc(&c->d_U, 2 * (size_t)D1 * M1 * sizeof(double2)));
   return SLDG_OK;
 }

@@ -56,6 +56,9 @@ struct SweepArgs {
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);  // FP64 FMA
 cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st);   // double-float
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
+// fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the layout does not fit
+cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
+                                 const void* ab2, const int* s2, cudaStream_t st);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
 
 }  // namespace sldg

@@ -178,21 +178,6 @@ __global__ void k_pois_fwd_x(const double* __restrict__ rho, const double2* __re
   }
 }
 
-// R[m2][m1] = sum_n2 F2[m2][n2] T[n2][m1];  block = m2, threads over m1
-__global__ void k_pois_fwd_y(const double2* __restrict__ T, const double2* __restrict__ F2, int D1,
-                             int M1, double2* __restrict__ R) {
-  const int m2 = blockIdx.x;
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int n2 = 0; n2 < D1; ++n2) {
-      const double2 t = cmul(F2[(long long)m2 * D1 + n2], T[(long long)n2 * M1 + m1]);
-      acc.x += t.x;
-      acc.y += t.y;
-    }
-    R[(long long)m2 * M1 + m1] = acc;
-  }
-}
-
 // multiplier c_d(m) = -i k_d m_d / |k m|^2 as the real q with c = -i q
 __device__ inline double pois_q(int d, int m1, int m2, double k0, double k1) {
   if (m1 == 0 && m2 == 0) return 0.0;
@@ -200,24 +185,42 @@ __device__ inline double pois_q(int d, int m1, int m2, double k0, double k1) {
   return (d == 0 ? a : b) / (a * a + b * b);
 }
 
-// U_d[n2][m1] = sum_m2 G2[n2][m2] c_d(m) R[m2][m1];  block = n2, threads m1
-__global__ void k_pois_inv_y(const double2* __restrict__ R, const double2* __restrict__ G2,
-                             int K1, int M1, long long ustride, double k0, double k1,
+// S_d[m2][m1] = c_d(m) rho_hat(m) with rho_hat(m) = sum_n2 F2[m2][n2] T[n2][m1];
+// block = m2, threads over m1 (the multipliers are applied once per mode)
+__global__ void k_pois_fwd_y(const double2* __restrict__ T, const double2* __restrict__ F2, int D1,
+                             int K1, int M1, long long sstride, double k0, double k1,
+                             double2* __restrict__ S) {
+  const int mi = blockIdx.x;
+  const int m2 = mi - K1;
+  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int n2 = 0; n2 < D1; ++n2) {
+      const double2 t = cmul(F2[(long long)mi * D1 + n2], T[(long long)n2 * M1 + m1]);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    // c r = -i q r = (q r.y, -q r.x)
+    const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
+    S[(long long)mi * M1 + m1] = make_double2(q0 * acc.y, -q0 * acc.x);
+    S[sstride + (long long)mi * M1 + m1] = make_double2(q1 * acc.y, -q1 * acc.x);
+  }
+}
+
+// U_d[n2][m1] = sum_m2 G2[n2][m2] S_d[m2][m1];  block = n2, threads over m1
+__global__ void k_pois_inv_y(const double2* __restrict__ S, const double2* __restrict__ G2,
+                             int M2, int M1, long long sstride, long long ustride,
                              double2* __restrict__ U) {
   const int n2 = blockIdx.x;
-  const int M2 = 2 * K1 + 1;
   for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
     double2 u0 = make_double2(0.0, 0.0), u1 = make_double2(0.0, 0.0);
     for (int mi = 0; mi < M2; ++mi) {
-      const int m2 = mi - K1;
-      const double2 r = R[(long long)mi * M1 + m1];
-      const double2 gr = cmul(G2[(long long)n2 * M2 + mi], r);
-      // c r = -i q r = (q r.y, -q r.x)
-      const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
-      u0.x += q0 * gr.y;
-      u0.y -= q0 * gr.x;
-      u1.x += q1 * gr.y;
-      u1.y -= q1 * gr.x;
+      const double2 g = G2[(long long)n2 * M2 + mi];
+      const double2 a = cmul(g, S[(long long)mi * M1 + m1]);
+      const double2 b = cmul(g, S[sstride + (long long)mi * M1 + m1]);
+      u0.x += a.x;
+      u0.y += a.y;
+      u1.x += b.x;
+      u1.y += b.y;
     }
     U[(long long)n2 * M1 + m1] = u0;
     U[ustride + (long long)n2 * M1 + m1] = u1;
@@ -527,8 +530,9 @@ cudaError_t launch_poisson(const PoissonArgs& a, const double* rho, double* E1, 
   const long long us = (long long)a.D1 * M1;
   const int t1 = M1 < 256 ? ((M1 + 31) / 32) * 32 : 256;
   k_pois_fwd_x<<<a.D1, t1, a.D0 * sizeof(double), st>>>(rho, a.F1, a.D0, M1, a.T);
-  k_pois_fwd_y<<<M2, t1, 0, st>>>(a.T, a.F2, a.D1, M1, a.R);
-  k_pois_inv_y<<<a.D1, t1, 0, st>>>(a.R, a.G2, a.K1, M1, us, a.k0, a.k1, a.U);
+  const long long ss = (long long)M2 * M1;
+  k_pois_fwd_y<<<M2, t1, 0, st>>>(a.T, a.F2, a.D1, a.K1, M1, ss, a.k0, a.k1, a.R);
+  k_pois_inv_y<<<a.D1, t1, 0, st>>>(a.R, a.G2, M2, M1, ss, us, a.U);
   const int t2 = a.D0 < 256 ? ((a.D0 + 31) / 32) * 32 : 256;
   k_pois_inv_x<<<a.D1, t2, 2 * M1 * sizeof(double2), st>>>(a.U, a.G1, a.D0, M1, us, E1, E2);
   *nlaunch += 4;

@@ -1,0 +1,222 @@
+// sweep_x12.cuh -- the two half drifts X1(tau/2), X2(tau/2) of FP32 storage
+// fused into one pass over f: one x-plane (fixed v1, v2: D1 rows of D0
+// values) per thread-block cluster of CS CTAs, each CTA holding D1/CS rows
+// in shared memory.
+//   1. every CTA stages its rows (cp.async, contiguous in f);
+//   2. X1 in place on its rows, warp per row pair (each lane reads all the
+//      source cells of its outputs into registers before the warp writes);
+//   3. cluster barrier: every CTA's X1 rows are final;
+//   4. X2 for the CTA's own rows: the source rows of an output cell (a few
+//      rows away, periodic in x2) are read from this CTA's shared memory or,
+//      across the row split, from the owning CTA's through distributed
+//      shared memory; outputs go straight to f as float2 rows;
+//   5. cluster barrier: no CTA leaves while a peer may still read its rows.
+// f is read once and written once for both sweeps.  The arithmetic of every
+// output is that of the separate packed kernels (sweep_f32x2.cuh).
+#pragma once
+
+#include "sweep_f32x2.cuh"
+
+namespace sldg {
+
+constexpr int kX12Threads = 256;
+constexpr int kX12Groups = 8;  // cell runs per column pair in the X2 phase
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" :::
+                   "memory");
+}
+// shared-memory address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_map(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster_f2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+
+// CPL: cells of an x1 line per lane (nc0 <= 32 CPL)
+template <int N, int CPL>
+__global__ void __launch_bounds__(kX12Threads, 3)
+    k_sweep_x12_f32(float* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
+                    const float* __restrict__ ab1, const int* __restrict__ s1,
+                    const float* __restrict__ ab2, const int* __restrict__ s2) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* rows = reinterpret_cast<float*>(smraw);
+  const int D0 = nc0 * N, D1 = nc1 * N;
+  const unsigned rank = cluster_ctarank();
+  const long long plane = blockIdx.x / cs;
+  const int cells_per = nc1 / cs;  // x2 cells held by one CTA
+  const int H = cells_per * N;     // rows held by one CTA
+  float* fp = f + plane * (long long)D1 * D0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  // 1. stage rows rank*H .. rank*H + H - 1
+  {
+    const float* src = fp + (long long)rank * H * D0;
+    const int chunks = H * D0 / 4;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 4 * i, src + 4 * i);
+    cp_async_wait_all();
+  }
+  const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
+  __syncthreads();
+
+  // 2. X1 in place, warp per row pair (the two lanes of every FP32x2 op)
+  {
+    float2 A[NN], B[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      const float a = ab1[(long long)i * D2 + key1], b = ab1[(long long)(NN + i) * D2 + key1];
+      A[i] = make_float2(a, a);
+      B[i] = make_float2(b, b);
+    }
+    const int sa = wrap_cell(-s1[key1] - 1, nc0);
+    const int cb = min(lane * CPL, nc0), ce = min(cb + CPL, nc0);
+    for (int p = wid; p < H / 2; p += nw) {
+      float* ra = rows + (2 * p) * D0;
+      float* rb = ra + D0;
+      float2 x[CPL + 1][N];
+      int k = cb + sa;
+      if (k >= nc0) k -= nc0;
+#pragma unroll
+      for (int t = 0; t <= CPL; ++t) {
+        if (cb + t <= ce) {  // source cells of outputs cb .. ce-1: cb+sa .. ce+sa
+#pragma unroll
+          for (int l = 0; l < N; ++l) x[t][l] = make_float2(ra[k * N + l], rb[k * N + l]);
+        }
+        k = k + 1 == nc0 ? 0 : k + 1;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < CPL; ++t) {
+        const int c = cb + t;
+        if (c < ce) {
+          float2 y[N];
+          f2_cell<N>(A, B, x[t], x[t + 1], y);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            ra[c * N + j] = y[j].x;
+            rb[c * N + j] = y[j].y;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // 3. every CTA's rows hold X1 f
+  cluster_sync();
+
+  // 4. X2 for rows rank*H .. rank*H + H - 1
+  {
+    float2 A[NN], B[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      const float a = ab2[(long long)i * D3 + key2], b = ab2[(long long)(NN + i) * D3 + key2];
+      A[i] = make_float2(a, a);
+      B[i] = make_float2(b, b);
+    }
+    const int sa = wrap_cell(-s2[key2] - 1, nc1);
+    const int npairs = D0 / 2;
+    const int items = npairs * kX12Groups;
+    auto load = [&](int kcell, int c0, float2* xv) {
+      const int owner = kcell / cells_per;
+      const int lrow = (kcell - owner * cells_per) * N;
+      if (owner == (int)rank) {
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+          xv[l] = *reinterpret_cast<const float2*>(rows + (lrow + l) * D0 + c0);
+      } else {
+        const unsigned base = cluster_map(rows + lrow * D0 + c0, (unsigned)owner);
+#pragma unroll
+        for (int l = 0; l < N; ++l) xv[l] = ld_cluster_f2(base + (unsigned)(l * D0 * 4));
+      }
+    };
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int q = it % npairs, g = it / npairs;
+      const int c0 = 2 * q;
+      const int lb = (g * cells_per) / kX12Groups, le = ((g + 1) * cells_per) / kX12Groups;
+      if (lb >= le) continue;
+      const int cglob = (int)rank * cells_per + lb;
+      int k = cglob + sa;
+      if (k >= nc1) k -= nc1;
+      float2 xa[N], xb[N];
+      load(k, c0, xa);
+      float* out = fp + (long long)(cglob * N) * D0 + c0;
+#pragma unroll 1
+      for (int c = lb; c < le; ++c, out += N * D0) {
+        k = k + 1 == nc1 ? 0 : k + 1;
+        load(k, c0, xb);
+        float2 y[N];
+        f2_cell<N>(A, B, xa, xb, y);
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2*>(out + j * D0) = y[j];
+#pragma unroll
+        for (int l = 0; l < N; ++l) xa[l] = xb[l];
+      }
+    }
+  }
+  // 5. peers may still read these rows
+  cluster_sync();
+}
+
+// Fused X1(frac) X2(frac) on FP32 storage; cudaErrorNotSupported when the
+// layout does not fit (the caller then runs the two sweeps).
+template <int N, int CPL>
+cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
+                         const int* s2, cudaStream_t st) {
+  const int nc0 = g.nc[0], nc1 = g.nc[1];
+  const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
+  const long long planes = g.D[2] * g.D[3];
+  if (D0 % 4 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
+  // the smallest cluster whose row share fits three CTAs per SM
+  int cs = 0;
+  for (int c = 2; c <= 8; c *= 2) {
+    if (nc1 % c) continue;
+    const long long H = (long long)(nc1 / c) * N;
+    if (H % 2 || (H * D0) % 4) continue;
+    if (H * D0 * (long long)sizeof(float) <= 75 * 1024) {
+      cs = c;
+      break;
+    }
+  }
+  if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
+  const size_t smem = (size_t)(nc1 / cs) * N * D0 * sizeof(float);
+  auto kfn = k_sweep_x12_f32<N, CPL>;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(planes * cs));
+  cfg.blockDim = dim3(kX12Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
+                            static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2);
+}
+
+template <int N>
+cudaError_t launch_x12_N(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
+                         const int* s2, cudaStream_t st) {
+  const int nc0 = g.nc[0];
+  if (nc0 <= 64) return launch_x12_T<N, 2>(f, g, ab1, s1, ab2, s2, st);
+  if (nc0 <= 128) return launch_x12_T<N, 4>(f, g, ab1, s1, ab2, s2, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace sldg

@@ -312,3 +312,20 @@ def test_host_batches_match_single_steps(lib, orc, prec):
     W0 = s.step_host_batches(host[1].contiguous(), 4)
     assert np.all(W0 == W[1])
     s.close()
+
+
+@pytest.mark.parametrize("deg,nc", [(2, (8, 8, 6, 5)), (1, (16, 12, 7, 6)), (2, (12, 16, 5, 4)),
+                                    (0, (36, 10, 9, 8))])
+def test_fp32_fused_x_pass_matches_separate_sweeps(lib, orc, deg, nc):
+    # one fused X1 X2 pass (thread-block clusters) gives the bits of the two
+    # separate sweeps; both stay within FP32 rounding of the oracle
+    outs = []
+    for flags in (0, lib._native.SLDG_FLAG_NO_XFUSION):
+        s, og = make(lib, orc, deg, nc, dt=0.1, prec="fp32", flags=flags)
+        s.set_initial(0, (0.5, 0.5, 0.5))
+        W = s.step(3, history=True)
+        outs.append((get(s), W))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref, Wr, _, _ = orc.step(og, orc.init(og, 0, (0.5, 0.5, 0.5)), 3)
+    assert relerr(outs[0][0], ref.reshape(og.shape)) < 1e-5
