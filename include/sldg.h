@@ -63,9 +63,10 @@ extern "C" {
                                    default double-float arithmetic on the FP32
                                    pipe (same results to ~1e-15; slower on GB300,
                                    whose FP64 pipe is about 1/64 of FP32) */
-#define SLDG_FLAG_NO_XFUSION 2  /* FP32 storage: run the X1 and X2 half drifts
-                                   as two sweeps instead of one fused pass over
-                                   each x-plane (same results, bit for bit) */
+#define SLDG_FLAG_NO_XFUSION 2  /* run the X1 and X2 half drifts as two sweeps
+                                   instead of one fused pass over each x-plane
+                                   (FP32: the same bits; FP64 double-float: the
+                                   same arithmetic to its rounding) */
 
 #define SLDG_VBC_ZERO_INFLOW 0 /* v-sweeps drop source cells outside the box */
 #define SLDG_VBC_PERIODIC 1    /* v-sweeps wrap (test mode: exact mass) */
@@ -85,7 +86,7 @@ extern "C" {
 #define SLDG_K_OTHER 7
 #define SLDG_K_ADJ_X 8
 #define SLDG_K_ADJ_V 9
-#define SLDG_K_X12 10 /* fused X1, X2 half drifts (FP32 storage) */
+#define SLDG_K_X12 10 /* fused X1, X2 half drifts */
 #define SLDG_NUM_KINDS 11
 
 typedef struct {

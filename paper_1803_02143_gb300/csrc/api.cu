@@ -357,16 +357,21 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // after the step; the five intermediate sub-step states in between are kept
 // as double-float (hi, lo) pairs in the same 8-byte elements, so the
 // conversion to and from the FP32 pipe's format happens once per step.
-// X1(tau/2) X2(tau/2) as one fused pass (FP32 storage); false when the
-// layout does not suit it and the two sweeps must run separately
-int run_x12(sldg_ctx* c, void* buf, bool* done) {
+// X1(tau/2) X2(tau/2) as one fused pass over each x-plane (FP32 storage,
+// or FP64 storage in double-float arithmetic); *done stays false when the
+// layout does not suit it and the two sweeps must run separately.
+int run_x12(sldg_ctx* c, void* buf, bool in_df, bool out_df, bool* done) {
   *done = false;
-  if (c->prec != SLDG_FP32 || (c->cfg.flags & SLDG_FLAG_NO_XFUSION)) return SLDG_OK;
+  if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64)) return SLDG_OK;
   SLDG_TRY(ensure_xmats(c, 0, 0.5));
   SLDG_TRY(ensure_xmats(c, 1, 0.5));
   KTimer t(c, SLDG_K_X12);
-  const cudaError_t e = launch_sweep_x12_f32(buf, c->g, c->xm[0].ab, c->xm[0].s, c->xm[1].ab,
-                                             c->xm[1].s, c->stream);
+  const cudaError_t e =
+      c->prec == SLDG_FP32
+          ? launch_sweep_x12_f32(buf, c->g, c->xm[0].ab, c->xm[0].s, c->xm[1].ab, c->xm[1].s,
+                                 c->stream)
+          : launch_sweep_x12_df(buf, c->g, c->xm[0].ab2, c->xm[0].s, c->xm[1].ab2, c->xm[1].s,
+                                in_df ? 1 : 0, out_df ? 1 : 0, c->stream);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -382,7 +387,7 @@ int run_x12(sldg_ctx* c, void* buf, bool* done) {
 int do_step(sldg_ctx* c, void* buf, double* Wslot) {
   const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
   bool fused = false;
-  SLDG_TRY(run_x12(c, buf, &fused));
+  SLDG_TRY(run_x12(c, buf, false, df, &fused));
   if (!fused) {
     SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
     SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
@@ -394,7 +399,7 @@ int do_step(sldg_ctx* c, void* buf, double* Wslot) {
   }
   SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
   SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_x12(c, buf, &fused));
+  SLDG_TRY(run_x12(c, buf, df, false, &fused));
   if (!fused) {
     SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
     SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));

@@ -59,6 +59,11 @@ cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 // fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the layout does not fit
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
                                  const void* ab2, const int* s2, cudaStream_t st);
+// the same for FP64 storage in double-float arithmetic (sweep_df.cu); ab1, ab2
+// are the (hi, lo) float-pair tables, in_df / out_df the element formats
+cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
+                                const void* ab2, const int* s2, int in_df, int out_df,
+                                cudaStream_t st);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
 
 }  // namespace sldg

@@ -5,6 +5,7 @@
 // runs the one-lane double-float kernels.
 #include "sweep_df2.cuh"
 #include "sweep_df3.cuh"
+#include "sweep_x12_df.cuh"
 
 namespace sldg {
 
@@ -15,6 +16,25 @@ cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st) {
   if (a.in_df) return launch_sweep_any<PolDFT<true, false>>(a, st);
   if (a.out_df) return launch_sweep_any<PolDFT<false, true>>(a, st);
   return launch_sweep_any<PolDFT<false, false>>(a, st);
+}
+
+cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
+                                const void* ab2, const int* s2, int in_df, int out_df,
+                                cudaStream_t st) {
+  double* d = static_cast<double*>(f);
+  auto go = [&](auto nt) -> cudaError_t {
+    constexpr int N = decltype(nt)::value;
+    if (in_df && out_df) return launch_x12_df_N<N, true, true>(d, g, ab1, s1, ab2, s2, st);
+    if (in_df) return launch_x12_df_N<N, true, false>(d, g, ab1, s1, ab2, s2, st);
+    if (out_df) return launch_x12_df_N<N, false, true>(d, g, ab1, s1, ab2, s2, st);
+    return launch_x12_df_N<N, false, false>(d, g, ab1, s1, ab2, s2, st);
+  };
+  switch (g.n) {
+    case 1: return go(std::integral_constant<int, 1>());
+    case 2: return go(std::integral_constant<int, 2>());
+    case 3: return go(std::integral_constant<int, 3>());
+    default: return cudaErrorNotSupported;
+  }
 }
 
 }  // namespace sldg

@@ -1,0 +1,207 @@
+// sweep_x12_df.cuh -- the fused X1, X2 half-drift pass of sweep_x12.cuh for
+// FP64 storage in packed double-float arithmetic (the operations of
+// sweep_df3.cuh).
+#pragma once
+
+#include "sweep_df3.cuh"
+#include "sweep_x12.cuh"
+
+namespace sldg {
+
+// ---------------------------------------------------------------------------
+// A CTA's rows arrive as 8-byte elements (IEEE doubles, or (hi, lo) pairs
+// when IN_DF); X1 (lanes = the two rows of a warp's row pair) writes its
+// outputs back in place as (h_k, h_k+1, l_k, l_k+1) column pairs, which is
+// the operand layout of X2 (lanes = two adjacent columns); X2 writes 8-byte
+// elements to f (pairs when OUT_DF).  Matrices: (hi, hi, lo, lo) float4 per
+// entry in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+template <int N, int CPL, bool IN_DF, bool OUT_DF>
+__global__ void __launch_bounds__(kX12Threads, 3)
+    k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
+                   const float2* __restrict__ ab1, const int* __restrict__ s1,
+                   const float2* __restrict__ ab2, const int* __restrict__ s2) {
+  constexpr int MN = 2 * N * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* m1 = reinterpret_cast<float4*>(smraw);
+  float4* m2 = m1 + MN;
+  double* rows = reinterpret_cast<double*>(m2 + MN);
+  const int D0 = nc0 * N, D1 = nc1 * N;
+  const unsigned rank = cluster_ctarank();
+  const long long plane = blockIdx.x / cs;
+  const int cells_per = nc1 / cs;
+  const int H = cells_per * N;
+  double* fp = f + plane * (long long)D1 * D0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  {
+    const double* src = fp + (long long)rank * H * D0;
+    const int chunks = H * D0 / 2;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 2 * i, src + 2 * i);
+  }
+  const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
+  for (int i = threadIdx.x; i < MN; i += blockDim.x) {
+    const float2 a = ab1[(long long)i * D2 + key1], b = ab2[(long long)i * D3 + key2];
+    m1[i] = make_float4(a.x, a.x, a.y, a.y);
+    m2[i] = make_float4(b.x, b.x, b.y, b.y);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // X1 in place, warp per row pair; outputs as column pairs
+  {
+    const int sa = wrap_cell(-s1[key1] - 1, nc0);
+    const int cb = min(lane * CPL, nc0), ce = min(cb + CPL, nc0);
+    for (int p = wid; p < H / 2; p += nw) {
+      double* ra = rows + (2 * p) * D0;
+      double* rb = ra + D0;
+      float2 xh[CPL + 1][N], xl[CPL + 1][N];
+      int k = cb + sa;
+      if (k >= nc0) k -= nc0;
+#pragma unroll
+      for (int t = 0; t <= CPL; ++t) {
+        if (cb + t <= ce) {
+#pragma unroll
+          for (int l = 0; l < N; ++l) {
+            float h0, l0, h1, l1;
+            load_pair<IN_DF>(ra[k * N + l], h0, l0);
+            load_pair<IN_DF>(rb[k * N + l], h1, l1);
+            xh[t][l] = make_float2(h0, h1);
+            xl[t][l] = make_float2(l0, l1);
+          }
+        }
+        k = k + 1 == nc0 ? 0 : k + 1;
+      }
+      __syncwarp();
+      float* fa = reinterpret_cast<float*>(ra);
+      float* fb = reinterpret_cast<float*>(rb);
+#pragma unroll
+      for (int t = 0; t < CPL; ++t) {
+        const int c = cb + t;
+        if (c < ce) {
+          float2 sh[N], sl[N];
+          df3_accumulate<N>(m1, xh[t], xl[t], xh[t + 1], xl[t + 1], sh, sl);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const int pos = c * N + j;
+            const int o = (pos >> 1) * 4 + (pos & 1);  // float slot of h in its column pair
+            fa[o] = sh[j].x;
+            fa[o + 2] = sl[j].x;
+            fb[o] = sh[j].y;
+            fb[o + 2] = sl[j].y;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  cluster_sync();
+
+  // X2 for the CTA's rows from column-pair operands
+  {
+    const int sa = wrap_cell(-s2[key2] - 1, nc1);
+    const int npairs = D0 / 2;
+    const int items = npairs * kX12Groups;
+    auto load = [&](int kcell, int c0, float2* xh, float2* xl) {
+      const int owner = kcell / cells_per;
+      const int lrow = (kcell - owner * cells_per) * N;
+      if (owner == (int)rank) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const float4 u = *reinterpret_cast<const float4*>(rows + (lrow + l) * D0 + c0);
+          xh[l] = make_float2(u.x, u.y);
+          xl[l] = make_float2(u.z, u.w);
+        }
+      } else {
+        const unsigned base = cluster_map(rows + lrow * D0 + c0, (unsigned)owner);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const float4 u = ld_cluster_f4(base + (unsigned)(l * D0 * 8));
+          xh[l] = make_float2(u.x, u.y);
+          xl[l] = make_float2(u.z, u.w);
+        }
+      }
+    };
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int q = it % npairs, g = it / npairs;
+      const int c0 = 2 * q;
+      const int lb = (g * cells_per) / kX12Groups, le = ((g + 1) * cells_per) / kX12Groups;
+      if (lb >= le) continue;
+      const int cglob = (int)rank * cells_per + lb;
+      int k = cglob + sa;
+      if (k >= nc1) k -= nc1;
+      float2 ah[N], al[N], bh[N], bl[N];
+      load(k, c0, ah, al);
+      double* out = fp + (long long)(cglob * N) * D0 + c0;
+#pragma unroll 1
+      for (int c = lb; c < le; ++c, out += N * D0) {
+        k = k + 1 == nc1 ? 0 : k + 1;
+        load(k, c0, bh, bl);
+        df3_cell<N, OUT_DF>(m2, ah, al, bh, bl, out, D0);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          ah[l] = bh[l];
+          al[l] = bl[l];
+        }
+      }
+    }
+  }
+  cluster_sync();
+}
+
+template <int N, int CPL, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int* s1,
+                            const void* ab2, const int* s2, cudaStream_t st) {
+  const int nc0 = g.nc[0], nc1 = g.nc[1];
+  const long long D0 = (long long)nc0 * N;
+  const long long planes = g.D[2] * g.D[3];
+  if (D0 % 2 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
+  const size_t mats = 2 * (size_t)(2 * N * N) * sizeof(float4);
+  int cs = 0;
+  for (int c = 2; c <= 8; c *= 2) {
+    if (nc1 % c) continue;
+    const long long H = (long long)(nc1 / c) * N;
+    if (H % 2) continue;
+    if (mats + H * D0 * (long long)sizeof(double) <= 75 * 1024) {
+      cs = c;
+      break;
+    }
+  }
+  if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
+  const size_t smem = mats + (size_t)(nc1 / cs) * N * D0 * sizeof(double);
+  auto kfn = k_sweep_x12_df<N, CPL, IN_DF, OUT_DF>;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(planes * cs));
+  cfg.blockDim = dim3(kX12Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
+                            static_cast<const float2*>(ab1), s1, static_cast<const float2*>(ab2),
+                            s2);
+}
+
+template <int N, bool IN_DF, bool OUT_DF>
+cudaError_t launch_x12_df_N(double* f, const Grid& g, const void* ab1, const int* s1,
+                            const void* ab2, const int* s2, cudaStream_t st) {
+  if (g.nc[0] <= 64) return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, g, ab1, s1, ab2, s2, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace sldg
