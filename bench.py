@@ -35,6 +35,8 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 FP64_FMA_PER_CLK_SM = 2   # FP64 FMA units per SM of GB300 (1.25 TFLOP/s nominal)
+FP32_LANES_PER_SM = 128   # FP32 operations per clock per SM
+DF_OPS_PER_MAC = 12       # FP32 operations per lane of a double-float multiply-accumulate
 SMS = 152
 
 
@@ -267,7 +269,21 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
     traffic = committed_traffic(f"{w.name}:{cfg.precision}:{kind}")
     hbm = {"achieved": algo_bytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": algo_bytes / avg_s / 1e9 / pk["hbm_gbs"], "peak_source": peak_src}
-    if cfg.precision == "fp64" and cfg.flags:
+    native = cfg.flags & 1
+    if cfg.precision == "fp64" and not native and kind == "x12":
+        # two double-float sweeps per byte: bound by FP32-pipe issue.  Each
+        # lane of a double-float multiply-accumulate is 12 FP32 operations
+        # (product, its FMA error, TwoSum, two low-word adds, two cross FMAs)
+        clk = pk.get("sm_max_mhz", 2070.0)
+        ops = 2 * cfg.numel * (2 * n) * DF_OPS_PER_MAC
+        peak_t = SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+        return {"bound": "alu", "achieved": ops / avg_s / 1e12, "peak": peak_t,
+                "unit": "T FP32 ops/s", "frac": ops / avg_s / 1e12 / peak_t, "traffic": traffic,
+                "kernel": f"sweep_{kind}",
+                "peak_source": "FP32 lanes x max SM clock (152 SMs x 128 lanes)",
+                "hbm": hbm, "avg_launch_ms": ms / cnt,
+                "per_kernel_ms_per_step": {k: v[0] / steps_timed for k, v in timing.items() if v[1]}}
+    if cfg.precision == "fp64" and native:
         clk = pk.get("sm_max_mhz", 2070.0)
         peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": algo_flops / avg_s / 1e12, "peak": peak_tf,
