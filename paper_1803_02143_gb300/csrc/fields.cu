@@ -160,22 +160,52 @@ __device__ inline double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// T[n2][m1] = sum_n1 F1[n1][m1] rho[n2][n1];  block = row n2, threads over m1
+// The maps are small dense products.  Each kernel takes one row per block
+// and sums over k for the block's outputs m with the k range split over
+// KS = blockDim / cols threads per output, combined in a fixed order, so
+// all SMs share the FP64 work instead of one warp per row.
+struct Acc4 {
+  double a, b, c, d;
+};
+__device__ inline Acc4 acc_add(Acc4 u, Acc4 v) { return {u.a + v.a, u.b + v.b, u.c + v.c, u.d + v.d}; }
+
+template <class Term, class Out>
+__device__ void block_split_sum(int cols, int K, Term term, Out out) {
+  __shared__ Acc4 red[256];
+  const int T = blockDim.x;  // <= 256
+  const int KS = max(1, min(T / max(cols, 1), K));
+  const int per = T / KS;
+  const int mi = threadIdx.x % per, ks = threadIdx.x / per;
+  for (int m0 = 0; m0 < cols; m0 += per) {
+    const int m = m0 + mi;
+    Acc4 acc = {0.0, 0.0, 0.0, 0.0};
+    if (ks < KS && m < cols)
+      for (int k = ks; k < K; k += KS) acc = acc_add(acc, term(m, k));
+    if (ks < KS) red[ks * per + mi] = acc;
+    __syncthreads();
+    if (ks == 0 && m < cols) {
+      Acc4 t = red[mi];
+      for (int q = 1; q < KS; ++q) t = acc_add(t, red[q * per + mi]);
+      out(m, t);
+    }
+    __syncthreads();
+  }
+}
+
+// T[n2][m1] = sum_n1 F1[n1][m1] rho[n2][n1];  block = row n2
 __global__ void k_pois_fwd_x(const double* __restrict__ rho, const double2* __restrict__ F1,
                              int D0, int M1, double2* __restrict__ T) {
   extern __shared__ double srow[];
   const int n2 = blockIdx.x;
   for (int i = threadIdx.x; i < D0; i += blockDim.x) srow[i] = rho[(long long)n2 * D0 + i];
   __syncthreads();
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int n1 = 0; n1 < D0; ++n1) {
-      const double2 w = F1[(long long)n1 * M1 + m1];
-      acc.x = fma(w.x, srow[n1], acc.x);
-      acc.y = fma(w.y, srow[n1], acc.y);
-    }
-    T[(long long)n2 * M1 + m1] = acc;
-  }
+  block_split_sum(
+      M1, D0,
+      [&](int m1, int n1) {
+        const double2 w = F1[(long long)n1 * M1 + m1];
+        return Acc4{w.x * srow[n1], w.y * srow[n1], 0.0, 0.0};
+      },
+      [&](int m1, Acc4 t) { T[(long long)n2 * M1 + m1] = make_double2(t.a, t.b); });
 }
 
 // multiplier c_d(m) = -i k_d m_d / |k m|^2 as the real q with c = -i q
@@ -186,48 +216,46 @@ __device__ inline double pois_q(int d, int m1, int m2, double k0, double k1) {
 }
 
 // S_d[m2][m1] = c_d(m) rho_hat(m) with rho_hat(m) = sum_n2 F2[m2][n2] T[n2][m1];
-// block = m2, threads over m1 (the multipliers are applied once per mode)
+// block = m2 (the multipliers are applied once per mode)
 __global__ void k_pois_fwd_y(const double2* __restrict__ T, const double2* __restrict__ F2, int D1,
                              int K1, int M1, long long sstride, double k0, double k1,
                              double2* __restrict__ S) {
   const int mi = blockIdx.x;
   const int m2 = mi - K1;
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int n2 = 0; n2 < D1; ++n2) {
-      const double2 t = cmul(F2[(long long)mi * D1 + n2], T[(long long)n2 * M1 + m1]);
-      acc.x += t.x;
-      acc.y += t.y;
-    }
-    // c r = -i q r = (q r.y, -q r.x)
-    const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
-    S[(long long)mi * M1 + m1] = make_double2(q0 * acc.y, -q0 * acc.x);
-    S[sstride + (long long)mi * M1 + m1] = make_double2(q1 * acc.y, -q1 * acc.x);
-  }
+  block_split_sum(
+      M1, D1,
+      [&](int m1, int n2) {
+        const double2 t = cmul(F2[(long long)mi * D1 + n2], T[(long long)n2 * M1 + m1]);
+        return Acc4{t.x, t.y, 0.0, 0.0};
+      },
+      [&](int m1, Acc4 r) {
+        // c r = -i q r = (q r.y, -q r.x)
+        const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
+        S[(long long)mi * M1 + m1] = make_double2(q0 * r.b, -q0 * r.a);
+        S[sstride + (long long)mi * M1 + m1] = make_double2(q1 * r.b, -q1 * r.a);
+      });
 }
 
-// U_d[n2][m1] = sum_m2 G2[n2][m2] S_d[m2][m1];  block = n2, threads over m1
+// U_d[n2][m1] = sum_m2 G2[n2][m2] S_d[m2][m1];  block = n2
 __global__ void k_pois_inv_y(const double2* __restrict__ S, const double2* __restrict__ G2,
                              int M2, int M1, long long sstride, long long ustride,
                              double2* __restrict__ U) {
   const int n2 = blockIdx.x;
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 u0 = make_double2(0.0, 0.0), u1 = make_double2(0.0, 0.0);
-    for (int mi = 0; mi < M2; ++mi) {
-      const double2 g = G2[(long long)n2 * M2 + mi];
-      const double2 a = cmul(g, S[(long long)mi * M1 + m1]);
-      const double2 b = cmul(g, S[sstride + (long long)mi * M1 + m1]);
-      u0.x += a.x;
-      u0.y += a.y;
-      u1.x += b.x;
-      u1.y += b.y;
-    }
-    U[(long long)n2 * M1 + m1] = u0;
-    U[ustride + (long long)n2 * M1 + m1] = u1;
-  }
+  block_split_sum(
+      M1, M2,
+      [&](int m1, int mi) {
+        const double2 g = G2[(long long)n2 * M2 + mi];
+        const double2 a = cmul(g, S[(long long)mi * M1 + m1]);
+        const double2 b = cmul(g, S[sstride + (long long)mi * M1 + m1]);
+        return Acc4{a.x, a.y, b.x, b.y};
+      },
+      [&](int m1, Acc4 t) {
+        U[(long long)n2 * M1 + m1] = make_double2(t.a, t.b);
+        U[ustride + (long long)n2 * M1 + m1] = make_double2(t.c, t.d);
+      });
 }
 
-// E_d[n2][n1] = Re U_d[n2][0] + 2 sum_{m1>=1} Re(G1[m1][n1] U_d[n2][m1])
+// E_d[n2][n1] = Re U_d[n2][0] + 2 sum_{m1>=1} Re(G1[m1][n1] U_d[n2][m1]);  block = n2
 __global__ void k_pois_inv_x(const double2* __restrict__ U, const double2* __restrict__ G1, int D0,
                              int M1, long long ustride, double* __restrict__ E1,
                              double* __restrict__ E2) {
@@ -238,20 +266,22 @@ __global__ void k_pois_inv_x(const double2* __restrict__ U, const double2* __res
     su[M1 + i] = U[ustride + (long long)n2 * M1 + i];
   }
   __syncthreads();
-  for (int n1 = threadIdx.x; n1 < D0; n1 += blockDim.x) {
-    double e0 = 0.0, e1 = 0.0;
-    for (int m1 = 1; m1 < M1; ++m1) {
-      const double2 g = G1[(long long)m1 * D0 + n1];
-      e0 += g.x * su[m1].x - g.y * su[m1].y;
-      e1 += g.x * su[M1 + m1].x - g.y * su[M1 + m1].y;
-    }
-    E1[(long long)n2 * D0 + n1] = su[0].x + 2.0 * e0;
-    E2[(long long)n2 * D0 + n1] = su[M1].x + 2.0 * e1;
-  }
+  block_split_sum(
+      D0, M1 - 1,
+      [&](int n1, int k) {
+        const int m1 = k + 1;
+        const double2 g = G1[(long long)m1 * D0 + n1];
+        return Acc4{g.x * su[m1].x - g.y * su[m1].y, g.x * su[M1 + m1].x - g.y * su[M1 + m1].y,
+                    0.0, 0.0};
+      },
+      [&](int n1, Acc4 t) {
+        E1[(long long)n2 * D0 + n1] = su[0].x + 2.0 * t.a;
+        E2[(long long)n2 * D0 + n1] = su[M1].x + 2.0 * t.b;
+      });
 }
 
 // ---- transpose of the Poisson map -------------------------------------------
-// V_d[n2][m1] = sum_n1 G1[m1][n1] Ebar_d[n2][n1];  block = n2, threads m1
+// V_d[n2][m1] = sum_n1 G1[m1][n1] Ebar_d[n2][n1];  block = n2
 __global__ void k_pois_adj_x(const double* __restrict__ Eb1, const double* __restrict__ Eb2,
                              const double2* __restrict__ G1, int D0, int M1, long long vstride,
                              double2* __restrict__ V) {
@@ -262,18 +292,17 @@ __global__ void k_pois_adj_x(const double* __restrict__ Eb1, const double* __res
     srow2[D0 + i] = Eb2[(long long)n2 * D0 + i];
   }
   __syncthreads();
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
-    for (int n1 = 0; n1 < D0; ++n1) {
-      const double2 g = G1[(long long)m1 * D0 + n1];
-      a.x = fma(g.x, srow2[n1], a.x);
-      a.y = fma(g.y, srow2[n1], a.y);
-      b.x = fma(g.x, srow2[D0 + n1], b.x);
-      b.y = fma(g.y, srow2[D0 + n1], b.y);
-    }
-    V[(long long)n2 * M1 + m1] = a;
-    V[vstride + (long long)n2 * M1 + m1] = b;
-  }
+  block_split_sum(
+      M1, D0,
+      [&](int m1, int n1) {
+        const double2 g = G1[(long long)m1 * D0 + n1];
+        const double e1 = srow2[n1], e2 = srow2[D0 + n1];
+        return Acc4{g.x * e1, g.y * e1, g.x * e2, g.y * e2};
+      },
+      [&](int m1, Acc4 t) {
+        V[(long long)n2 * M1 + m1] = make_double2(t.a, t.b);
+        V[vstride + (long long)n2 * M1 + m1] = make_double2(t.c, t.d);
+      });
 }
 
 // P[m2][m1] = sum_d c_d(m) sum_n2 G2[n2][m2] V_d[n2][m1];  block = m2
@@ -283,21 +312,19 @@ __global__ void k_pois_adj_y(const double2* __restrict__ V, const double2* __res
   const int mi = blockIdx.x;
   const int m2 = mi - K1;
   const int M2 = 2 * K1 + 1;
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 h0 = make_double2(0.0, 0.0), h1 = make_double2(0.0, 0.0);
-    for (int n2 = 0; n2 < D1; ++n2) {
-      const double2 g = G2[(long long)n2 * M2 + mi];
-      const double2 a = cmul(g, V[(long long)n2 * M1 + m1]);
-      const double2 b = cmul(g, V[vstride + (long long)n2 * M1 + m1]);
-      h0.x += a.x;
-      h0.y += a.y;
-      h1.x += b.x;
-      h1.y += b.y;
-    }
-    const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
-    // c h = -i q h = (q h.y, -q h.x)
-    P[(long long)mi * M1 + m1] = make_double2(q0 * h0.y + q1 * h1.y, -(q0 * h0.x + q1 * h1.x));
-  }
+  block_split_sum(
+      M1, D1,
+      [&](int m1, int n2) {
+        const double2 g = G2[(long long)n2 * M2 + mi];
+        const double2 a = cmul(g, V[(long long)n2 * M1 + m1]);
+        const double2 b = cmul(g, V[vstride + (long long)n2 * M1 + m1]);
+        return Acc4{a.x, a.y, b.x, b.y};
+      },
+      [&](int m1, Acc4 h) {
+        const double q0 = pois_q(0, m1, m2, k0, k1), q1 = pois_q(1, m1, m2, k0, k1);
+        // c h = -i q h = (q h.y, -q h.x)
+        P[(long long)mi * M1 + m1] = make_double2(q0 * h.b + q1 * h.d, -(q0 * h.a + q1 * h.c));
+      });
 }
 
 // Y[p2][m1] = sum_m2 F2[m2][p2] P[m2][m1];  block = p2
@@ -305,15 +332,13 @@ __global__ void k_pois_adj_y2(const double2* __restrict__ P, const double2* __re
                               int K1, int M1, double2* __restrict__ Y) {
   const int p2 = blockIdx.x;
   const int M2 = 2 * K1 + 1;
-  for (int m1 = threadIdx.x; m1 < M1; m1 += blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int mi = 0; mi < M2; ++mi) {
-      const double2 t = cmul(F2[(long long)mi * D1 + p2], P[(long long)mi * M1 + m1]);
-      acc.x += t.x;
-      acc.y += t.y;
-    }
-    Y[(long long)p2 * M1 + m1] = acc;
-  }
+  block_split_sum(
+      M1, M2,
+      [&](int m1, int mi) {
+        const double2 t = cmul(F2[(long long)mi * D1 + p2], P[(long long)mi * M1 + m1]);
+        return Acc4{t.x, t.y, 0.0, 0.0};
+      },
+      [&](int m1, Acc4 t) { Y[(long long)p2 * M1 + m1] = make_double2(t.a, t.b); });
 }
 
 // rhobar[p2][p1] = Re sum_{m1} wt(m1) F1[p1][m1] Y[p2][m1], wt = 1 (m1 = 0), 2
@@ -323,15 +348,17 @@ __global__ void k_pois_adj_x2(const double2* __restrict__ Y, const double2* __re
   const int p2 = blockIdx.x;
   for (int i = threadIdx.x; i < M1; i += blockDim.x) sy[i] = Y[(long long)p2 * M1 + i];
   __syncthreads();
-  for (int p1 = threadIdx.x; p1 < D0; p1 += blockDim.x) {
-    double acc = 0.0;
-    for (int m1 = 1; m1 < M1; ++m1) {
-      const double2 w = F1[(long long)p1 * M1 + m1];
-      acc += w.x * sy[m1].x - w.y * sy[m1].y;
-    }
-    const double2 w0 = F1[(long long)p1 * M1];
-    rhob[(long long)p2 * D0 + p1] = (w0.x * sy[0].x - w0.y * sy[0].y) + 2.0 * acc;
-  }
+  block_split_sum(
+      D0, M1 - 1,
+      [&](int p1, int k) {
+        const int m1 = k + 1;
+        const double2 w = F1[(long long)p1 * M1 + m1];
+        return Acc4{w.x * sy[m1].x - w.y * sy[m1].y, 0.0, 0.0, 0.0};
+      },
+      [&](int p1, Acc4 t) {
+        const double2 w0 = F1[(long long)p1 * M1];
+        rhob[(long long)p2 * D0 + p1] = (w0.x * sy[0].x - w0.y * sy[0].y) + 2.0 * t.a;
+      });
 }
 
 // ---------------------------------------------------------------------------
@@ -494,11 +521,11 @@ cudaError_t launch_build_mats(int prec, long long count, const double* src, doub
                               cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (prec == SLDG_FP64)
-    k_build_mats<double><<<nblk(count, 128), 128, 0, st>>>(count, src, dt, frac, h, b,
+    k_build_mats<double><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
                                                            (double*)ab, (double*)dab,
                                                            (float2*)ab2, s);
   else
-    k_build_mats<float><<<nblk(count, 128), 128, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
+    k_build_mats<float><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
                                                           (float*)dab, nullptr, s);
   return cudaGetLastError();
 }
@@ -528,12 +555,11 @@ cudaError_t launch_poisson(const PoissonArgs& a, const double* rho, double* E1, 
                            cudaStream_t st, int* nlaunch) {
   const int M1 = a.K0 + 1, M2 = 2 * a.K1 + 1;
   const long long us = (long long)a.D1 * M1;
-  const int t1 = M1 < 256 ? ((M1 + 31) / 32) * 32 : 256;
+  const int t1 = 256, t2 = 256;
   k_pois_fwd_x<<<a.D1, t1, a.D0 * sizeof(double), st>>>(rho, a.F1, a.D0, M1, a.T);
   const long long ss = (long long)M2 * M1;
   k_pois_fwd_y<<<M2, t1, 0, st>>>(a.T, a.F2, a.D1, a.K1, M1, ss, a.k0, a.k1, a.R);
   k_pois_inv_y<<<a.D1, t1, 0, st>>>(a.R, a.G2, M2, M1, ss, us, a.U);
-  const int t2 = a.D0 < 256 ? ((a.D0 + 31) / 32) * 32 : 256;
   k_pois_inv_x<<<a.D1, t2, 2 * M1 * sizeof(double2), st>>>(a.U, a.G1, a.D0, M1, us, E1, E2);
   *nlaunch += 4;
   return cudaGetLastError();
@@ -543,12 +569,11 @@ cudaError_t launch_poisson_adj(const PoissonArgs& a, const double* Eb1, const do
                                double* rhob, cudaStream_t st, int* nlaunch) {
   const int M1 = a.K0 + 1, M2 = 2 * a.K1 + 1;
   const long long vs = (long long)a.D1 * M1;
-  const int t1 = M1 < 256 ? ((M1 + 31) / 32) * 32 : 256;
+  const int t1 = 256, t2 = 256;
   // V uses a.U (2 x D1 x M1), P uses a.R (M2 x M1), Y uses a.T (D1 x M1)
   k_pois_adj_x<<<a.D1, t1, 2 * a.D0 * sizeof(double), st>>>(Eb1, Eb2, a.G1, a.D0, M1, vs, a.U);
   k_pois_adj_y<<<M2, t1, 0, st>>>(a.U, a.G2, a.D1, a.K1, M1, vs, a.k0, a.k1, a.R);
   k_pois_adj_y2<<<a.D1, t1, 0, st>>>(a.R, a.F2, a.D1, a.K1, M1, a.T);
-  const int t2 = a.D0 < 256 ? ((a.D0 + 31) / 32) * 32 : 256;
   k_pois_adj_x2<<<a.D1, t2, M1 * sizeof(double2), st>>>(a.T, a.F1, a.D0, M1, rhob);
   *nlaunch += 4;
   return cudaGetLastError();
