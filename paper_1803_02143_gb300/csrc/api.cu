@@ -167,8 +167,10 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_wv2);
   dfree(c->d_wx);
   for (int d = 0; d < 2; ++d) {
-    dfree(c->xm[d].ab); dfree(c->xm[d].dab); dfree(c->xm[d].ab2); dfree(c->xm[d].s);
-    dfree(c->vm[d].ab); dfree(c->vm[d].dab); dfree(c->vm[d].ab2); dfree(c->vm[d].s);
+    for (MatSet* m : {&c->xm[d], &c->vm[d]}) {
+      dfree(m->ab); dfree(m->dab); dfree(m->ab2); dfree(m->s);
+      dfree(m->abt); dfree(m->abt2); dfree(m->st);
+    }
     dfree(c->d_E[d]);
     dfree(c->d_Eb[d]);
   }
@@ -207,7 +209,7 @@ PoissonArgs poisson_args(sldg_ctx* c) {
 }
 
 // ---- matrices -------------------------------------------------------------------
-int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv) {
+int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv, bool trans) {
   const size_t nn = (size_t)c->g.n * c->g.n;
   if (!m->ab) {
     SLDG_TRY(dalloc(&m->ab, 2 * nn * count * c->esize));
@@ -216,35 +218,46 @@ int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv) {
     m->count = count;
   }
   if (deriv && !m->dab) SLDG_TRY(dalloc(&m->dab, 2 * nn * count * c->esize));
+  if (trans && !m->abt) {
+    SLDG_TRY(dalloc(&m->abt, 2 * nn * count * c->esize));
+    SLDG_TRY(dalloc(&m->st, count * sizeof(int)));
+    if (c->prec == SLDG_FP64) SLDG_TRY(dalloc(&m->abt2, 2 * nn * count * sizeof(float2)));
+  }
   return SLDG_OK;
 }
 
-// x-sweep d (0 or 1): one matrix pair per node of v_{d+1}, shift v dt frac
-int ensure_xmats(sldg_ctx* c, int d, double frac) {
+// x-sweep d (0 or 1): one matrix pair per node of v_{d+1}, shift v dt frac;
+// trans: also the transposed tables of the adjoint
+int ensure_xmats(sldg_ctx* c, int d, double frac, bool trans = false) {
   MatSet& m = c->xm[d];
-  if (m.valid && m.frac == frac) return SLDG_OK;
+  if (m.valid && m.frac == frac && (!trans || m.with_t)) return SLDG_OK;
   const int vd = d + 2;
-  SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false));
+  SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false, trans));
   KTimer t(c, SLDG_K_VMAT);
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], c->basis,
-                            m.ab, nullptr, m.ab2, m.s, c->stream));
+                            m.ab, nullptr, m.ab2, m.s, c->stream, trans ? m.abt : nullptr,
+                            trans ? m.abt2 : nullptr, trans ? m.st : nullptr));
   m.frac = frac;
   m.valid = true;
+  m.with_t = trans;
   return SLDG_OK;
 }
 
 // v-sweep d (0 or 1 for v1, v2): one pair per x-node, shift E_d dt frac
-int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv) {
+int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv, bool trans = false) {
   MatSet& m = c->vm[d];
   if (!c->have_field) return SLDG_ERR_STATE;
-  if (m.valid && m.frac == frac && (!deriv || m.with_deriv)) return SLDG_OK;
-  SLDG_TRY(alloc_matset(c, &m, c->g.Dx, deriv));
+  if (m.valid && m.frac == frac && (!deriv || m.with_deriv) && (!trans || m.with_t)) return SLDG_OK;
+  SLDG_TRY(alloc_matset(c, &m, c->g.Dx, deriv, trans));
   KTimer t(c, SLDG_K_VMAT);
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], c->basis,
-                            m.ab, deriv ? m.dab : nullptr, m.ab2, m.s, c->stream));
+                            m.ab, deriv ? m.dab : nullptr, m.ab2, m.s, c->stream,
+                            trans ? m.abt : nullptr, trans ? m.abt2 : nullptr,
+                            trans ? m.st : nullptr));
   m.frac = frac;
   m.valid = true;
   m.with_deriv = deriv;
+  m.with_t = trans;
   return SLDG_OK;
 }
 
@@ -264,24 +277,29 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   a.nc = g.nc[dim];
   a.adjoint = adjoint ? 1 : 0;
   const bool ebar = adjoint && dim >= 2 && gfwd && Ebar;
+  const bool native = (c->cfg.flags & SLDG_FLAG_NATIVE_FP64) != 0;
+  // a transposed sweep without the shift derivative runs the forward kernels
+  // on the transposed tables ([B^T; A^T], shift entries -s - 1)
+  const bool tform = adjoint && !ebar && !(c->prec == SLDG_FP64 && native);
   MatSet* m;
   if (dim < 2) {
-    SLDG_TRY(ensure_xmats(c, dim, frac));
+    SLDG_TRY(ensure_xmats(c, dim, frac, tform));
     m = &c->xm[dim];
     a.periodic = 1;
   } else {
-    SLDG_TRY(ensure_vmats(c, dim - 2, frac, ebar));
+    SLDG_TRY(ensure_vmats(c, dim - 2, frac, ebar, tform));
     m = &c->vm[dim - 2];
     a.periodic = g.vbc == SLDG_VBC_PERIODIC;
   }
-  a.ab = m->ab;
-  a.ab2 = m->ab2;
+  a.ab = tform ? m->abt : m->ab;
+  a.ab2 = tform ? m->abt2 : m->ab2;
   a.dab = m->dab;
-  a.native_fp64 = (c->cfg.flags & SLDG_FLAG_NATIVE_FP64) ? 1 : 0;
+  a.native_fp64 = native ? 1 : 0;
   a.in_df = in_df ? 1 : 0;
   a.out_df = out_df ? 1 : 0;
-  a.s = m->s;
+  a.s = tform ? m->st : m->s;
   a.mcount = m->count;
+  if (tform) a.adjoint = 0;
   switch (dim) {
     case 0:
       a.inner = 1;

@@ -20,6 +20,12 @@ struct MatSet {
   void* dab = nullptr;  // same precision, derivative matrices
   void* ab2 = nullptr;  // FP64 contexts: (hi, lo) float pairs of ab, same layout
   int* s = nullptr;
+  // transposed sweep in forward form: [B^T; A^T] applied to source cells
+  // c + s and c + s + 1, i.e. shift entries -s - 1 (built on demand)
+  void* abt = nullptr;   // context precision
+  void* abt2 = nullptr;  // FP64 contexts: (hi, lo) float pairs
+  int* st = nullptr;
+  bool with_t = false;
   long long count = 0;
   double frac = 0.0;    // shift scale these matrices were built for
   bool valid = false;

@@ -62,7 +62,8 @@ template <typename T>
 __global__ void k_build_mats(long long count, const double* __restrict__ src, double dt,
                              double frac, double h, Basis b, T* __restrict__ ab,
                              T* __restrict__ dab, float2* __restrict__ ab2,
-                             int* __restrict__ svec) {
+                             int* __restrict__ svec, T* __restrict__ abt,
+                             float2* __restrict__ abt2, int* __restrict__ st) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= count) return;
   const double a = __dmul_rn(__dmul_rn(src[e], dt), frac);
@@ -85,8 +86,20 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
       dab[(long long)i * count + e] = (T)dA[i];
       dab[(long long)(nn + i) * count + e] = (T)dB[i];
     }
+    if (abt) {  // [B^T; A^T]: entry i = j n + l holds B[l][j], then A[l][j]
+      const int j = i / b.n, l = i - j * b.n;
+      const double bt = B[l * b.n + j], at = A[l * b.n + j];
+      abt[(long long)i * count + e] = (T)bt;
+      abt[(long long)(nn + i) * count + e] = (T)at;
+      if (abt2) {
+        const float bh = (float)bt, ah = (float)at;
+        abt2[(long long)i * count + e] = make_float2(bh, (float)(bt - (double)bh));
+        abt2[(long long)(nn + i) * count + e] = make_float2(ah, (float)(at - (double)ah));
+      }
+    }
   }
   svec[e] = s;
+  if (st) st[e] = -s - 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -518,15 +531,17 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 
 cudaError_t launch_build_mats(int prec, long long count, const double* src, double dt, double frac,
                               double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
-                              cudaStream_t st) {
+                              cudaStream_t st, void* abt, void* abt2, int* sT) {
   if (count <= 0) return cudaSuccess;
   if (prec == SLDG_FP64)
     k_build_mats<double><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
                                                            (double*)ab, (double*)dab,
-                                                           (float2*)ab2, s);
+                                                           (float2*)ab2, s, (double*)abt,
+                                                           (float2*)abt2, sT);
   else
     k_build_mats<float><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
-                                                          (float*)dab, nullptr, s);
+                                                          (float*)dab, nullptr, s, (float*)abt,
+                                                          nullptr, sT);
   return cudaGetLastError();
 }
 
