@@ -168,7 +168,7 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_wx);
   for (int d = 0; d < 2; ++d) {
     for (MatSet* m : {&c->xm[d], &c->vm[d]}) {
-      dfree(m->ab); dfree(m->dab); dfree(m->ab2); dfree(m->s);
+      dfree(m->ab); dfree(m->dab); dfree(m->dab2); dfree(m->ab2); dfree(m->s);
       dfree(m->abt); dfree(m->abt2); dfree(m->st);
     }
     dfree(c->d_E[d]);
@@ -217,7 +217,10 @@ int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv, bool trans
     if (c->prec == SLDG_FP64) SLDG_TRY(dalloc(&m->ab2, 2 * nn * count * sizeof(float2)));
     m->count = count;
   }
-  if (deriv && !m->dab) SLDG_TRY(dalloc(&m->dab, 2 * nn * count * c->esize));
+  if (deriv && !m->dab) {
+    SLDG_TRY(dalloc(&m->dab, 2 * nn * count * c->esize));
+    if (c->prec == SLDG_FP64) SLDG_TRY(dalloc(&m->dab2, 2 * nn * count * sizeof(float2)));
+  }
   if (trans && !m->abt) {
     SLDG_TRY(dalloc(&m->abt, 2 * nn * count * c->esize));
     SLDG_TRY(dalloc(&m->st, count * sizeof(int)));
@@ -253,7 +256,7 @@ int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv, bool trans = false
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], c->basis,
                             m.ab, deriv ? m.dab : nullptr, m.ab2, m.s, c->stream,
                             trans ? m.abt : nullptr, trans ? m.abt2 : nullptr,
-                            trans ? m.st : nullptr));
+                            trans ? m.st : nullptr, deriv ? m.dab2 : nullptr));
   m.frac = frac;
   m.valid = true;
   m.with_deriv = deriv;
@@ -280,7 +283,10 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   const bool native = (c->cfg.flags & SLDG_FLAG_NATIVE_FP64) != 0;
   // a transposed sweep without the shift derivative runs the forward kernels
   // on the transposed tables ([B^T; A^T], shift entries -s - 1)
-  const bool tform = adjoint && !ebar && !(c->prec == SLDG_FP64 && native);
+  // FP64 double-float: the shift derivative is a separate kernel on the
+  // adjoint before the sweep, and the sweep itself runs in forward form
+  const bool ebar_df = ebar && c->prec == SLDG_FP64 && !native;
+  const bool tform = adjoint && (!ebar || ebar_df) && !(c->prec == SLDG_FP64 && native);
   MatSet* m;
   if (dim < 2) {
     SLDG_TRY(ensure_xmats(c, dim, frac, tform));
@@ -294,6 +300,7 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   a.ab = tform ? m->abt : m->ab;
   a.ab2 = tform ? m->abt2 : m->ab2;
   a.dab = m->dab;
+  a.dab2 = m->dab2;
   a.native_fp64 = native ? 1 : 0;
   a.in_df = in_df ? 1 : 0;
   a.out_df = out_df ? 1 : 0;
@@ -332,6 +339,22 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
     a.epart = c->d_epart;
   }
   const int kind = adjoint ? (dim < 2 ? SLDG_K_ADJ_X : SLDG_K_ADJ_V) : SLDG_K_X1 + dim;
+  if (ebar_df) {  // partials of d/dE <lam, S g> from the adjoint before the sweep
+    KTimer t(c, kind);
+    SweepArgs ae = a;
+    ae.s = m->s;  // the forward shifts (a carries the transposed form)
+    const cudaError_t e = launch_ebar_df(ae, c->stream);
+    if (e == cudaErrorNotSupported) {  // layout not taken: the fused FP64 FMA kernel
+      t.n = 0;
+      a.ab = m->ab;
+      a.ab2 = m->ab2;
+      a.s = m->s;
+      a.adjoint = 1;
+    } else if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SLDG_ERR_CUDA;
+    }
+  }
   {
     KTimer t(c, kind);
     cudaError_t e;

@@ -22,6 +22,7 @@ struct MatSet {
   int* s = nullptr;
   // transposed sweep in forward form: [B^T; A^T] applied to source cells
   // c + s and c + s + 1, i.e. shift entries -s - 1 (built on demand)
+  void* dab2 = nullptr;  // FP64 contexts: (hi, lo) float pairs of dab
   void* abt = nullptr;   // context precision
   void* abt2 = nullptr;  // FP64 contexts: (hi, lo) float pairs
   int* st = nullptr;
@@ -46,6 +47,7 @@ struct SweepArgs {
   const void* ab;      // matrices (SoA), see MatSet
   const void* ab2;     // the same matrices as (hi, lo) float pairs (FP64 contexts)
   const void* dab;
+  const void* dab2;    // (hi, lo) pairs of dab (FP64 contexts)
   const int* s;
   long long mcount;    // keys in the matrix set
   long long key_div;   // x-sweeps: key = (line or block index / key_div) % key_mod
@@ -61,6 +63,9 @@ struct SweepArgs {
 // Kernel launchers (sweep_f64.cu / sweep_f32.cu).
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);  // FP64 FMA
 cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st);   // double-float
+// shift-derivative partials of an adjoint v-sweep in double-float (a.f = the
+// adjoint before the sweep, a.g = the forward input, a.dab2, a.s, a.epart)
+cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 // fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the layout does not fit
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,

@@ -63,7 +63,8 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
                              double frac, double h, Basis b, T* __restrict__ ab,
                              T* __restrict__ dab, float2* __restrict__ ab2,
                              int* __restrict__ svec, T* __restrict__ abt,
-                             float2* __restrict__ abt2, int* __restrict__ st) {
+                             float2* __restrict__ abt2, int* __restrict__ st,
+                             float2* __restrict__ dab2) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= count) return;
   const double a = __dmul_rn(__dmul_rn(src[e], dt), frac);
@@ -85,6 +86,11 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
     if (dab) {
       dab[(long long)i * count + e] = (T)dA[i];
       dab[(long long)(nn + i) * count + e] = (T)dB[i];
+      if (dab2) {
+        const float ah = (float)dA[i], bh = (float)dB[i];
+        dab2[(long long)i * count + e] = make_float2(ah, (float)(dA[i] - (double)ah));
+        dab2[(long long)(nn + i) * count + e] = make_float2(bh, (float)(dB[i] - (double)bh));
+      }
     }
     if (abt) {  // [B^T; A^T]: entry i = j n + l holds B[l][j], then A[l][j]
       const int j = i / b.n, l = i - j * b.n;
@@ -531,17 +537,17 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 
 cudaError_t launch_build_mats(int prec, long long count, const double* src, double dt, double frac,
                               double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
-                              cudaStream_t st, void* abt, void* abt2, int* sT) {
+                              cudaStream_t st, void* abt, void* abt2, int* sT, void* dab2) {
   if (count <= 0) return cudaSuccess;
   if (prec == SLDG_FP64)
     k_build_mats<double><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
                                                            (double*)ab, (double*)dab,
                                                            (float2*)ab2, s, (double*)abt,
-                                                           (float2*)abt2, sT);
+                                                           (float2*)abt2, sT, (float2*)dab2);
   else
     k_build_mats<float><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
                                                           (float*)dab, nullptr, s, (float*)abt,
-                                                          nullptr, sT);
+                                                          nullptr, sT, nullptr);
   return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ struct PoissonArgs {
 cudaError_t launch_build_mats(int prec, long long count, const double* src, double dt, double frac,
                               double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
                               cudaStream_t st, void* abt = nullptr, void* abt2 = nullptr,
-                              int* sT = nullptr);
+                              int* sT = nullptr, void* dab2 = nullptr);
 cudaError_t launch_rho(int prec, const void* f, const Grid& g, const float2* wv2, double* part,
                        int chunks, double* rho, cudaStream_t st, int* nlaunch, int df = 0);
 cudaError_t launch_sum_rows(const double* part, int rows, long long cols, double scale, double* out,

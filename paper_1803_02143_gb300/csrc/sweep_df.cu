@@ -18,6 +18,15 @@ cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st) {
   return launch_sweep_any<PolDFT<false, false>>(a, st);
 }
 
+cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st) {
+  switch (a.n) {
+    case 1: return launch_ebar_df3_T<1>(a, st);
+    case 2: return launch_ebar_df3_T<2>(a, st);
+    case 3: return launch_ebar_df3_T<3>(a, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
                                 cudaStream_t st) {

@@ -602,4 +602,164 @@ cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Shift-derivative partials of an adjoint v-sweep (double-float): for every
+// column (x-node) and outer index o of the strided form,
+//   sum over cells c and nodes j of  lam[c][j] (A' g[c+sa] + B' g[c+sa+1])_j,
+// sa = -s-1 the forward source offset, lam the adjoint before the
+// transposed sweep, g the forward input; one partial per (o, column) to
+// epart[o * ncols + column], summed over o by the caller.  Both tiles are
+// staged and converted to column pairs like the sweep tiles; the per-thread
+// double-float partials are joined to FP64 and reduced over the cell runs in
+// a fixed order.
+// ---------------------------------------------------------------------------
+template <int N>
+inline size_t ebar_df3_smem(long long D) {
+  return (size_t)kDf3Pairs * df3_mat_stride<N>() * sizeof(float4) +
+         2 * (size_t)(D + N) * kStridedW * sizeof(double) +
+         (size_t)kDf3Groups * kStridedW * sizeof(double);
+}
+
+template <int N, bool PERIODIC>
+__global__ void __launch_bounds__(kDf3Threads, 2)
+    k_ebar_df3(const double* __restrict__ lam, const double* __restrict__ gf,
+               double* __restrict__ epart, int ncols, long long rstride, long long ostride, int nc,
+               int outer, const float2* __restrict__ dab2, const int* __restrict__ svec,
+               long long mcount) {
+  constexpr int W = kStridedW;
+  constexpr int MN = 2 * N * N;
+  constexpr int MS = df3_mat_stride<N>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* smat = reinterpret_cast<float4*>(smraw);
+  const int D = nc * N;
+  const int bstride = (D + N) * W;
+  double* tl = reinterpret_cast<double*>(smraw + (size_t)kDf3Pairs * MS * sizeof(float4));
+  double* tg = tl + bstride;
+  double* red = tg + bstride;  // [groups][W]
+  const int col0 = blockIdx.x * W;
+  const int nvalid = min(W, ncols - col0);
+  const int q = threadIdx.x % kDf3Pairs, g = threadIdx.x / kDf3Pairs;
+  const int c0 = 2 * q;
+  const int cb = (g * nc) / kDf3Groups, ce = ((g + 1) * nc) / kDf3Groups;
+  const bool active = c0 < nvalid && cb < ce;
+
+  for (int e = threadIdx.x; e < kDf3Pairs * MN; e += blockDim.x) {
+    const int pq = e / MN, i = e - pq * MN;
+    const int k0 = min(col0 + 2 * pq, ncols - 1), k1 = min(col0 + 2 * pq + 1, ncols - 1);
+    const float2 a0 = dab2[(long long)i * mcount + k0], a1 = dab2[(long long)i * mcount + k1];
+    smat[pq * MS + i] = make_float4(a0.x, a1.x, a0.y, a1.y);
+  }
+  int sa0 = -svec[min(col0 + c0, ncols - 1)] - 1;
+  int sa1 = -svec[min(col0 + c0 + 1, ncols - 1)] - 1;
+  if (PERIODIC) {
+    sa0 = wrap_cell(sa0, nc);
+    sa1 = wrap_cell(sa1, nc);
+  }
+  if (!PERIODIC)
+    for (int i = threadIdx.x; i < N * W; i += blockDim.x) tg[D * W + i] = 0.0;
+  const float4* M = smat + q * MS;
+  const int chunks = D * (W / 2);
+  const int vchunks = nvalid / 2;
+  auto row = [nc](int k) {
+    if (PERIODIC) return k;
+    return (unsigned)k < (unsigned)nc ? k : nc;
+  };
+  for (int o = blockIdx.y; o < outer; o += gridDim.y) {
+    const long long base = (long long)o * ostride + col0;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+      const int r = i / (W / 2), cq = i - r * (W / 2);
+      if (cq < vchunks) {
+        cp_async16(tl + r * W + 2 * cq, lam + base + r * rstride + 2 * cq);
+        cp_async16(tg + r * W + 2 * cq, gf + base + r * rstride + 2 * cq);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    df3_pair_planar<false>(tl, D * (W / 2));
+    df3_pair_planar<false>(tg, D * (W / 2));
+    __syncthreads();
+    float2 ph = make_float2(0.0f, 0.0f), pl = make_float2(0.0f, 0.0f);  // per-lane partial
+    bool first = true;
+    if (active) {
+      int k0 = cb + sa0, k1 = cb + sa1;
+      if (PERIODIC) {
+        if (k0 >= nc) k0 -= nc;
+        if (k1 >= nc) k1 -= nc;
+      }
+      float2 ah[N], al[N], bh[N], bl[N];
+      df3_load_cell<N, false>(tg, c0, row(k0), row(k1), ah, al);
+#pragma unroll 1
+      for (int c = cb; c < ce; ++c) {
+        k0 = PERIODIC ? (k0 + 1 == nc ? 0 : k0 + 1) : k0 + 1;
+        k1 = PERIODIC ? (k1 + 1 == nc ? 0 : k1 + 1) : k1 + 1;
+        df3_load_cell<N, false>(tg, c0, row(k0), row(k1), bh, bl);
+        float2 zh[N], zl[N];
+        df3_accumulate<N>(M, ah, al, bh, bl, zh, zl);
+        float2 lh[N], ll[N];
+        df3_load_cell<N, true>(tl, c0, c, c, lh, ll);  // lam at cell c, both lanes
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          if (first) {
+            df2_first(lh[j], ll[j], zh[j], zl[j], ph, pl);
+            first = false;
+          } else {
+            df2_mac(lh[j], ll[j], zh[j], zl[j], ph, pl);
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          ah[l] = bh[l];
+          al[l] = bl[l];
+        }
+      }
+    }
+    red[g * W + c0] = djoin_fast(ph.x, pl.x);
+    red[g * W + c0 + 1] = djoin_fast(ph.y, pl.y);
+    __syncthreads();
+    if (threadIdx.x < nvalid) {
+      double t = 0.0;
+      for (int gg = 0; gg < kDf3Groups; ++gg) t += red[gg * W + threadIdx.x];
+      epart[(long long)o * ncols + col0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <int N>
+cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
+  const double* lam = reinterpret_cast<const double*>(a.f);
+  const double* gf = reinterpret_cast<const double*>(a.g);
+  const long long D = (long long)a.nc * N;
+  long long ncols, rstride, ostride, outer;
+  if (a.dim == 3) {
+    ncols = a.key_mod;
+    rstride = a.inner;
+    ostride = a.key_mod;
+    outer = a.inner / a.key_mod;
+  } else if (a.dim == 2) {
+    ncols = a.inner;
+    rstride = a.inner;
+    ostride = D * a.inner;
+    outer = a.outer;
+  } else {
+    return cudaErrorNotSupported;
+  }
+  if (ncols != a.key_mod || ((ncols | rstride | ostride) & 1) ||
+      ((reinterpret_cast<uintptr_t>(lam) | reinterpret_cast<uintptr_t>(gf)) & 15) ||
+      ncols > 0x7fffffffLL - kStridedW || outer > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
+    return cudaErrorNotSupported;
+  const size_t smem = ebar_df3_smem<N>(D);
+  if (smem > 113 * 1024) return cudaErrorNotSupported;
+  const long long ncolblk = (ncols + kStridedW - 1) / kStridedW;
+  long long gy = (outer + kDf3TilesPerCtaV - 1) / kDf3TilesPerCtaV;
+  if (gy > 65535) gy = 65535;
+  auto kfn = a.periodic ? k_ebar_df3<N, true> : k_ebar_df3<N, false>;
+  cudaError_t e = set_smem(kfn, smem);
+  if (e != cudaSuccess) return e;
+  kfn<<<dim3((unsigned)ncolblk, (unsigned)gy), kDf3Threads, smem, st>>>(
+      lam, gf, a.epart, (int)ncols, rstride, ostride, a.nc, (int)outer,
+      reinterpret_cast<const float2*>(a.dab2), a.s, a.mcount);
+  return cudaGetLastError();
+}
+
 }  // namespace sldg
