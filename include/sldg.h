@@ -233,13 +233,16 @@ int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
  * of the context precision).  J_out (host, nullable) receives J.  f is left
  * at the recorded final state.
  * Memory: besides the checkpoint pool, two copies of f for the forward
- * intermediates of one step and up to ckpt_every - 1 recomputation slots
+ * intermediates of one step and up to 2 ckpt_every + 1 recomputation slots
  * (copies of f), as many as fit in the free device memory less a margin
- * (and at most the limit of sldg_set_slot_limit).  With every slot a segment
- * is recomputed once; with fewer, the segment is bisected recursively and
- * its states are recomputed about log2(ckpt_every) times; with one slot,
- * from the checkpoint for every step.  The gradient is the same whatever
- * the number of slots (the same arithmetic, only repeated).
+ * (and at most the limit of sldg_set_slot_limit).  With 2 S + 1 slots for a
+ * segment of S steps, one forward pass keeps every step's intermediates
+ * (the inputs of V1 and V2 and the kick field); with S - 1, the segment's
+ * states are kept and each step's intermediates rebuilt; with fewer, the
+ * segment is bisected recursively and its states are recomputed about
+ * log2(ckpt_every) times; with one slot, from the checkpoint for every
+ * step.  The gradient is the same whatever the number of slots (the same
+ * arithmetic, only repeated).
  * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits), CUDA. */
 int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
 

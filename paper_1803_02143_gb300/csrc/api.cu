@@ -178,7 +178,7 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_F1); dfree(c->d_F2); dfree(c->d_G1); dfree(c->d_G2);
   dfree(c->d_T); dfree(c->d_R); dfree(c->d_U);
   dfree(c->d_W); dfree(c->d_diag); dfree(c->d_Wrec); dfree(c->d_rhob); dfree(c->d_epart);
-  dfree(c->d_ckpool); dfree(c->d_seg);
+  dfree(c->d_ckpool); dfree(c->d_seg); dfree(c->d_Ecap);
   for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
   dfree(c->d_alt);
   for (int i = 0; i < 2; ++i) {
@@ -439,6 +439,51 @@ int do_step(sldg_ctx* c, void* buf, double* Wslot) {
     SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream));
   }
   SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
+  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
+  SLDG_TRY(run_x12(c, buf, df, false, &fused));
+  if (!fused) {
+    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
+    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
+  }
+  return SLDG_OK;
+}
+
+// Step m of the forward again from its state in buf, keeping what the
+// adjoint of the step needs: g2 (the input of V1, after the x half drifts),
+// g3 (the input of V2, after V1) as IEEE doubles, and the kick field (E_out,
+// 2 D_0 D_1 doubles, nullable; the context's field holds it as well).  buf
+// follows exactly the states of do_step (the same kernels and formats), so a
+// recomputed trajectory is the recorded one bit for bit.  g3_out may be buf
+// itself when !full (converted in place).  full: finish the step in buf.
+int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_out, bool full) {
+  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+  const size_t fb = c->g.N * c->esize;
+  auto take = [&](void* dst) -> int {  // IEEE copy of the current state
+    if (df) {
+      SLDG_CU(launch_df_to_ieee(buf, dst, c->g.N, c->stream));
+      c->launches += 1;
+    } else if (dst != buf) {
+      SLDG_CU(cudaMemcpyAsync(dst, buf, fb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return SLDG_OK;
+  };
+  bool fused = false;
+  SLDG_TRY(run_x12(c, buf, false, df, &fused));
+  if (!fused) {
+    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
+    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
+  }
+  SLDG_TRY(compute_fields(c, buf, df));
+  if (E_out) {
+    SLDG_CU(cudaMemcpyAsync(E_out, c->d_E[0], c->g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    SLDG_CU(cudaMemcpyAsync(E_out + c->g.Dx, c->d_E[1], c->g.Dx * sizeof(double),
+                            cudaMemcpyDeviceToDevice, c->stream));
+  }
+  SLDG_TRY(take(g2_out));
+  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
+  if (!full) return take(g3_out);
+  SLDG_TRY(take(g3_out));
   SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
   SLDG_TRY(run_x12(c, buf, df, false, &fused));
   if (!fused) {
@@ -888,22 +933,23 @@ int sldg_backward_stats(const sldg_ctx* c, long long* recomputed_steps, int* slo
 
 namespace {
 
-// Adjoint of Strang step m (global index) from its initial state fm:
-// grad <- (step m)^T grad + dJ/dW_m c_m contributions (Eq. AB-sldg transposed,
-// the v-shift derivatives, the Poisson and charge-density adjoints).
-int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad) {
+// Adjoint of Strang step m (global index) from its forward intermediates g2
+// (input of V1) and g3 (input of V2) and its kick field (E: 2 D_0 D_1
+// doubles, or null when the context's field is already the step's):
+// grad <- (step m)^T grad + the dJ/dW_m c_m contributions (Eq. AB-sldg
+// transposed, the v-shift derivatives, the Poisson and charge-density
+// adjoints).
+int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double* E, int m,
+                      const double* cW, void* grad) {
   const Grid& g = c->g;
-  const size_t fb = g.N * c->esize;
-  void* g2 = c->d_work[0];
-  void* g3 = c->d_work[1];
-  // forward intermediates: g2 = X2 X1 f^m (input of V1), g3 = V1 g2 (input of V2)
-  SLDG_CU(cudaMemcpyAsync(g2, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
-  SLDG_TRY(run_sweep(c, g2, 0, 0.5, false, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, g2, 1, 0.5, false, nullptr, nullptr));
-  SLDG_TRY(compute_fields(c, g2));
-  SLDG_CU(cudaMemcpyAsync(g3, g2, fb, cudaMemcpyDeviceToDevice, c->stream));
-  SLDG_TRY(run_sweep(c, g3, 2, 1.0, false, nullptr, nullptr));
-  // reverse
+  if (E) {
+    SLDG_CU(cudaMemcpyAsync(c->d_E[0], E, g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    SLDG_CU(cudaMemcpyAsync(c->d_E[1], E + g.Dx, g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    c->have_field = true;
+    invalidate_vmats(c);
+  }
   SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
   SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
   SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
@@ -929,6 +975,17 @@ int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* gra
   return SLDG_OK;
 }
 
+// The same from the step's initial state fm (recomputing g2, g3 and the
+// field in the two work buffers)
+int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad) {
+  const size_t fb = c->g.N * c->esize;
+  void* g2 = c->d_work[0];
+  void* g3 = c->d_work[1];
+  SLDG_CU(cudaMemcpyAsync(g3, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
+  SLDG_TRY(forward_stage(c, g3, g2, g3, nullptr, false));
+  return adjoint_step_from(c, g2, g3, nullptr, m, cW, grad);
+}
+
 // dst <- src advanced by k Strang steps
 int advance(sldg_ctx* c, void* dst, const void* src, int k) {
   const size_t fb = c->g.N * c->esize;
@@ -950,6 +1007,23 @@ int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>
   const size_t fb = c->g.N * c->esize;
   const int n = b - a;
   if (n == 1) return adjoint_step(c, src, a, cW, grad);
+  if ((size_t)(2 * n + 1) <= free.size() && c->d_Ecap && n <= c->Ecap_steps) {
+    // one forward pass over the range keeps every step's g2, g3 and field
+    std::vector<char*> st(free.end() - (2 * n + 1), free.end());
+    free.resize(free.size() - (2 * n + 1));
+    char* w = st[2 * n];
+    SLDG_CU(cudaMemcpyAsync(w, src, fb, cudaMemcpyDeviceToDevice, c->stream));
+    const long long e2 = 2 * c->g.Dx;
+    for (int i = 0; i < n; ++i) {
+      SLDG_TRY(forward_stage(c, w, st[2 * i], st[2 * i + 1], c->d_Ecap + i * e2, i + 1 < n));
+      if (i + 1 < n) c->bwd_recomputed += 1;
+    }
+    for (int m = b - 1; m >= a; --m)
+      SLDG_TRY(adjoint_step_from(c, st[2 * (m - a)], st[2 * (m - a) + 1],
+                                 c->d_Ecap + (m - a) * e2, m, cW, grad));
+    free.insert(free.end(), st.begin(), st.end());
+    return SLDG_OK;
+  }
   if ((size_t)(n - 1) <= free.size()) {  // store states a+1 .. b-1, then walk back
     std::vector<char*> st(free.end() - (n - 1), free.end());
     free.resize(free.size() - (n - 1));
@@ -1011,7 +1085,14 @@ int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
   for (int i = 0; i < 2; ++i)
     if (!c->d_work[i]) SLDG_TRY(dalloc(&c->d_work[i], fb));
   SLDG_TRY(ensure_adjoint_scratch(c));
-  const size_t want = (size_t)std::max(1, std::min(ck, n) - 1);
+  // as many slots as a segment can use: 2 S + 1 keep every step's g2, g3
+  const size_t want = (size_t)(2 * std::min(ck, n) + 1);
+  if (!c->d_Ecap || c->Ecap_steps < std::min(ck, n)) {
+    dfree(c->d_Ecap);
+    c->Ecap_steps = 0;
+    SLDG_TRY(dalloc(&c->d_Ecap, (size_t)std::min(ck, n) * 2 * g.Dx * sizeof(double)));
+    c->Ecap_steps = std::min(ck, n);
+  }
   size_t slots = want;
   if (c->slot_limit > 0) slots = std::min(slots, (size_t)c->slot_limit);
   if (c->seg_count != slots) {

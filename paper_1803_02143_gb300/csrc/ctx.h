@@ -134,6 +134,8 @@ struct sldg_ctx {
   void* d_seg = nullptr;        // recomputation slots, seg_count states of f
   size_t seg_count = 0;
   int slot_limit = 0;           // upper bound on seg_count (0: as many as fit)
+  double* d_Ecap = nullptr;     // kick fields of a recomputed segment, [steps][2][Dx]
+  int Ecap_steps = 0;
   long long bwd_recomputed = 0; // Strang steps recomputed by the last backward
   double* d_Eb[2] = {nullptr, nullptr};
   double* d_rhob = nullptr;

@@ -530,6 +530,15 @@ __global__ void k_energy_adj(double* __restrict__ Eb1, double* __restrict__ Eb2,
   Eb2[p] += c * wx[p] * E2[p];
 }
 
+// dst = the IEEE doubles of the double-float pairs in src (dst may be src)
+__global__ void k_df_to_ieee(const double* src, double* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 p = df_unpack(src[i]);
+    dst[i] = djoin(p.x, p.y);
+  }
+}
+
 // ===========================================================================
 // Host launchers.
 // ===========================================================================
@@ -647,6 +656,12 @@ cudaError_t launch_param_grad(int prec, const void* grad, const Grid& g, int kin
     k_param_grad_partial<float><<<nb, 256, 0, st>>>((const float*)grad, g, kind, tab, part);
   k_ksum_final<<<1, 32, 0, st>>>(part, nb, out);
   *nlaunch += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_ieee(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_df_to_ieee<<<reduce_blocks() * 8, 256, 0, st>>>(static_cast<const double*>(src),
+                                                    static_cast<double*>(dst), n);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ def test_gradient_independent_of_slot_limit(lib, orc):
     n, ck = 13, 6
     grads, stats = [], []
     with lib.Sldg(cfg) as s:
-        for limit in (0, 1, 2, 3):
+        for limit in (0, 1, 2, 3, 5):
             s.set_slot_limit(limit)
             s.set_initial(0, params)
             s.record(n, ck)
@@ -60,9 +60,12 @@ def test_gradient_independent_of_slot_limit(lib, orc):
             stats.append(s.backward_stats())
     for g in grads[1:]:
         assert np.array_equal(g, grads[0])
-    # every slot: each segment recomputed once (5 + 5 + 0 steps); one slot:
-    # every state from its checkpoint (1 + 2 + ... + 5 per full segment)
-    assert stats[0] == (10, 5)
+    # 2 S + 1 = 13 slots: one pass per segment keeps every step's forward
+    # intermediates (5 + 5 + 0 steps recomputed); S - 1 = 5 slots: the
+    # segment's states are stored and each step's intermediates rebuilt; one
+    # slot: every state from its checkpoint (1 + 2 + ... + 5 per segment)
+    assert stats[0] == (10, 13)
+    assert stats[4] == (10, 5)
     assert stats[1] == (30, 1)
     assert stats[2][1] == 2 and 10 < stats[2][0] < 30
     _, gr, _ = orc.backward(og, orc.init(og, 0, params), n, ck)
