@@ -182,6 +182,11 @@ void free_all(sldg_ctx* c) {
   for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
   dfree(c->d_alt);
   for (int i = 0; i < 2; ++i) {
+    if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
+    c->step_graph[i] = nullptr;
+  }
+  dfree(c->d_counter);
+  for (int i = 0; i < 2; ++i) {
     if (c->ev_up[i]) cudaEventDestroy(c->ev_up[i]);
     if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
     c->ev_up[i] = c->ev_free[i] = nullptr;
@@ -425,7 +430,7 @@ int run_x12(sldg_ctx* c, void* buf, bool in_df, bool out_df, bool* done) {
   return SLDG_OK;
 }
 
-int do_step(sldg_ctx* c, void* buf, double* Wslot) {
+int do_step(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter = nullptr) {
   const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
   bool fused = false;
   SLDG_TRY(run_x12(c, buf, false, df, &fused));
@@ -436,7 +441,7 @@ int do_step(sldg_ctx* c, void* buf, double* Wslot) {
   SLDG_TRY(compute_fields(c, buf, df));
   if (Wslot) {
     KTimer t(c, SLDG_K_OTHER);
-    SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream));
+    SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream, Wcounter));
   }
   SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
   SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
@@ -489,6 +494,65 @@ int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_
   if (!fused) {
     SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
     SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
+  }
+  return SLDG_OK;
+}
+
+// nsteps Strang steps of f as replays of one recorded step (a CUDA graph),
+// W of each step to Wbase[counter++] (nullable; the device counter restarts
+// at 0 when reset_counter).  *replayed stays false when graphs do not apply
+// (fewer than two steps, per-kernel timing on, or an earlier capture failed)
+// and the caller runs the steps eagerly.
+int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed) {
+  const int hv = Wbase ? 1 : 0;
+  *replayed = false;
+  if (nsteps >= 2 && !c->timing && !c->graphs_off) {
+    // one recorded step replayed nsteps times: the launch overhead of the
+    // small kernels goes away on small grids
+    // everything the step allocates lazily exists before the capture
+    SLDG_TRY(ensure_xmats(c, 0, 0.5));
+    SLDG_TRY(ensure_xmats(c, 1, 0.5));
+    for (int d = 0; d < 2; ++d) SLDG_TRY(alloc_matset(c, &c->vm[d], c->g.Dx, false, false));
+    if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
+    if (c->step_graph[hv] && (c->step_graph_buf[hv] != c->f || c->step_graph_W[hv] != Wbase)) {
+      cudaGraphExecDestroy(c->step_graph[hv]);
+      c->step_graph[hv] = nullptr;
+    }
+    if (!c->step_graph[hv]) {
+      const long long l0 = c->launches;
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      const int rc = ok ? do_step(c, c->f, Wbase, hv ? c->d_counter : nullptr) : SLDG_ERR_CUDA;
+      if (ok) ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && rc == SLDG_OK;
+      if (ok) ok = cudaGraphInstantiate(&c->step_graph[hv], graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      c->step_graph_launches[hv] = c->launches - l0;
+      c->launches = l0;
+      if (!ok) {
+        cudaGetLastError();
+        if (c->step_graph[hv]) cudaGraphExecDestroy(c->step_graph[hv]);
+        c->step_graph[hv] = nullptr;
+        c->graphs_off = true;
+        invalidate_vmats(c);
+        c->have_field = false;
+      } else {
+        c->step_graph_buf[hv] = c->f;
+        c->step_graph_W[hv] = Wbase;
+      }
+    }
+    if (c->step_graph[hv]) {
+      if (hv && reset_counter) SLDG_CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
+      for (int m = 0; m < nsteps; ++m) {
+        SLDG_CU(cudaGraphLaunch(c->step_graph[hv], c->stream));
+        c->launches += c->step_graph_launches[hv];
+        c->t += c->g.dt;
+        c->step += 1;
+      }
+      // the context's field and v-matrices belong to the last replayed step
+      c->have_field = true;
+      invalidate_vmats(c);
+      *replayed = true;
+    }
   }
   return SLDG_OK;
 }
@@ -722,11 +786,14 @@ int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
   if (!c) return SLDG_ERR_BAD_PTR;
   if (nsteps < 0) return SLDG_ERR_ARG;
   if (W_history) SLDG_TRY(ensure_W(c, nsteps));
-  for (int m = 0; m < nsteps; ++m) {
-    SLDG_TRY(do_step(c, c->f, W_history ? c->d_W + m : nullptr));
-    c->t += c->g.dt;
-    c->step += 1;
-  }
+  bool replayed = false;
+  SLDG_TRY(replay_steps(c, nsteps, W_history ? c->d_W : nullptr, true, &replayed));
+  if (!replayed)
+    for (int m = 0; m < nsteps; ++m) {
+      SLDG_TRY(do_step(c, c->f, W_history ? c->d_W + m : nullptr));
+      c->t += c->g.dt;
+      c->step += 1;
+    }
   if (W_history && nsteps > 0) {
     SLDG_CU(cudaMemcpyAsync(W_history, c->d_W, nsteps * sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream));
@@ -895,14 +962,22 @@ int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   c->ck_count = nck;
   c->rec_t0 = c->t;
   c->rec_step0 = c->step;
-  for (int m = 0; m < nsteps; ++m) {
-    if (m % ckpt_every == 0) {
-      char* dst = reinterpret_cast<char*>(c->d_ckpool) + (size_t)(m / ckpt_every) * fb;
-      SLDG_CU(cudaMemcpyAsync(dst, c->f, fb, cudaMemcpyDeviceToDevice, c->stream));
+  for (int m0 = 0; m0 < nsteps; m0 += ckpt_every) {
+    char* dst = reinterpret_cast<char*>(c->d_ckpool) + (size_t)(m0 / ckpt_every) * fb;
+    SLDG_CU(cudaMemcpyAsync(dst, c->f, fb, cudaMemcpyDeviceToDevice, c->stream));
+    const int ns = std::min(ckpt_every, nsteps - m0);
+    bool replayed = false;
+    if (ns >= 2 && !c->timing && !c->graphs_off) {
+      if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
+      SLDG_CU(launch_set_int(c->d_counter, m0, c->stream));  // W of step m0 + i to d_Wrec[m0 + i]
+      SLDG_TRY(replay_steps(c, ns, c->d_Wrec, false, &replayed));
     }
-    SLDG_TRY(do_step(c, c->f, c->d_Wrec + m));
-    c->t += c->g.dt;
-    c->step += 1;
+    if (!replayed)
+      for (int m = m0; m < m0 + ns; ++m) {
+        SLDG_TRY(do_step(c, c->f, c->d_Wrec + m));
+        c->t += c->g.dt;
+        c->step += 1;
+      }
   }
   if (W_history) {
     SLDG_CU(cudaMemcpyAsync(W_history, c->d_Wrec, nsteps * sizeof(double), cudaMemcpyDeviceToHost,

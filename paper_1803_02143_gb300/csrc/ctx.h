@@ -154,6 +154,15 @@ struct sldg_ctx {
   double* h_W = nullptr;
   int h_W_cap = 0;
 
+  // sldg_step as a replayed CUDA graph of one Strang step (two variants:
+  // without / with the W history, whose slot comes from a device counter)
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  const void* step_graph_buf[2] = {nullptr, nullptr};  // f and W history they were made for
+  const void* step_graph_W[2] = {nullptr, nullptr};
+  long long step_graph_launches[2] = {0, 0};
+  bool graphs_off = false;  // a capture failed: steps run eagerly from then on
+  int* d_counter = nullptr;
+
   // state
   double t = 0.0;
   long long step = 0;

@@ -383,14 +383,25 @@ __global__ void k_pois_adj_x2(const double2* __restrict__ Y, const double2* __re
 // ---------------------------------------------------------------------------
 // Electric energy W = 1/2 sum_x w_x (E1^2 + E2^2), one block, written to out.
 // ---------------------------------------------------------------------------
+// counter (nullable): out is a history and W goes to out[*counter], which is
+// then advanced (steps replayed from one recorded graph fill consecutive slots)
 __global__ void k_energy(const double* __restrict__ E1, const double* __restrict__ E2,
-                         const double* __restrict__ wx, long long Dx, double* __restrict__ out) {
+                         const double* __restrict__ wx, long long Dx, double* __restrict__ out,
+                         int* __restrict__ counter) {
   __shared__ KSum shm[32];
   KSum k[1] = {{0.0, 0.0}};
   for (long long p = threadIdx.x; p < Dx; p += blockDim.x)
     kadd(k[0], 0.5 * wx[p] * (E1[p] * E1[p] + E2[p] * E2[p]));
   block_ksum<1>(k, shm);
-  if (threadIdx.x == 0) *out = k[0].s + k[0].c;
+  if (threadIdx.x == 0) {
+    if (counter) {
+      const int i = *counter;
+      out[i] = k[0].s + k[0].c;
+      *counter = i + 1;
+    } else {
+      *out = k[0].s + k[0].c;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -530,6 +541,8 @@ __global__ void k_energy_adj(double* __restrict__ Eb1, double* __restrict__ Eb2,
   Eb2[p] += c * wx[p] * E2[p];
 }
 
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
 // dst = the IEEE doubles of the double-float pairs in src (dst may be src)
 __global__ void k_df_to_ieee(const double* src, double* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -610,8 +623,8 @@ cudaError_t launch_poisson_adj(const PoissonArgs& a, const double* Eb1, const do
 }
 
 cudaError_t launch_energy(const double* E1, const double* E2, const double* wx, long long Dx,
-                          double* out, cudaStream_t st) {
-  k_energy<<<1, 256, 0, st>>>(E1, E2, wx, Dx, out);
+                          double* out, cudaStream_t st, int* counter) {
+  k_energy<<<1, 256, 0, st>>>(E1, E2, wx, Dx, out, counter);
   return cudaGetLastError();
 }
 
@@ -656,6 +669,11 @@ cudaError_t launch_param_grad(int prec, const void* grad, const Grid& g, int kin
     k_param_grad_partial<float><<<nb, 256, 0, st>>>((const float*)grad, g, kind, tab, part);
   k_ksum_final<<<1, 32, 0, st>>>(part, nb, out);
   *nlaunch += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st) {
+  k_set_int<<<1, 1, 0, st>>>(p, v);
   return cudaGetLastError();
 }
 

@@ -22,14 +22,17 @@ cudaError_t launch_rho(int prec, const void* f, const Grid& g, const float2* wv2
                        int chunks, double* rho, cudaStream_t st, int* nlaunch, int df = 0);
 cudaError_t launch_sum_rows(const double* part, int rows, long long cols, double scale, double* out,
                             int accumulate, cudaStream_t st);
+// *p = v on the stream
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 // double-float pairs -> IEEE doubles, n elements (in place when dst == src)
 cudaError_t launch_df_to_ieee(const void* src, void* dst, long long n, cudaStream_t st);
 cudaError_t launch_poisson(const PoissonArgs& a, const double* rho, double* E1, double* E2,
                            cudaStream_t st, int* nlaunch);
 cudaError_t launch_poisson_adj(const PoissonArgs& a, const double* Eb1, const double* Eb2,
                                double* rhob, cudaStream_t st, int* nlaunch);
+// counter (device, nullable): W goes to out[*counter], which is then advanced
 cudaError_t launch_energy(const double* E1, const double* E2, const double* wx, long long Dx,
-                          double* out, cudaStream_t st);
+                          double* out, cudaStream_t st, int* counter = nullptr);
 size_t diag_scratch_doubles();
 cudaError_t launch_diag(int prec, const void* f, const Grid& g, const double* wx, const double* wv,
                         const double* z2, const double* z3, double* scratch, double* out4,

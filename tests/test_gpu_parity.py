@@ -337,3 +337,24 @@ def test_fused_x_pass_matches_separate_sweeps(lib, orc, deg, nc, prec):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     ref, Wr, _, _ = orc.step(og, orc.init(og, 0, (0.5, 0.5, 0.5)), 3)
     assert relerr(outs[0][0], ref.reshape(og.shape)) < (1e-5 if prec == "fp32" else 3 * TOL64_STEP)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_graph_replay_matches_eager_steps(lib, orc, prec):
+    # sldg_step(n >= 2) replays one recorded step (a CUDA graph); single
+    # steps run eagerly: the same bits, W history included, also when the
+    # context switches between the two and between history and none
+    res = []
+    for graph in (True, False):
+        s, og = make(lib, orc, 2, (8, 6, 10, 12), dt=0.1, prec=prec)
+        s.set_initial(0, (0.5, 0.5, 0.5))
+        if graph:
+            W = np.concatenate([s.step(4, history=True), s.step(3, history=True)])
+            s.step(2)
+        else:
+            W = np.concatenate([s.step(1, history=True) for _ in range(7)])
+            s.step(1)
+            s.step(1)
+        res.append((get(s), W))
+        s.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
