@@ -1,6 +1,6 @@
-"""The five workloads: the paper's Landau damping and two-stream problems
+"""The workloads: the paper's Landau damping and two-stream problems
 (Sec. 4, Eq. (iv-nl); Sec. 5, Eq. (iv-tsi)) at the sizes this library is
-measured on.
+measured on, and the paper's own dG4 runs (Sec. 4, Sec. 5, Table 1).
 """
 from __future__ import annotations
 
@@ -14,6 +14,8 @@ LANDAU_LO = (0.0, 0.0, -6.0, -6.0)
 LANDAU_HI = (4 * math.pi, 4 * math.pi, 6.0, 6.0)
 TSI_LO = (0.0, 0.0, -9.0, -9.0)
 TSI_HI = (10 * math.pi, 10 * math.pi, 9.0, 9.0)
+TSI_PAPER_LO = (0.0, 0.0, -6.0, -6.0)
+TSI_PAPER_HI = (10 * math.pi, 10 * math.pi, 6.0, 6.0)
 
 
 @dataclass(frozen=True)
@@ -53,6 +55,21 @@ WORKLOADS = {
         "two_stream_64x128",
         Config(degree=2, ncell=(64, 64, 128, 128), lo=TSI_LO, hi=TSI_HI, dt=0.05),
         N.SLDG_INIT_TWO_STREAM, (1e-3, 0.2, 3.0), 800),
+    # the paper's dG4 (degree 3) runs of Sec. 4 and Table 1: nonlinear Landau
+    # damping, dt 0.1 to T = 50, at 64, 128 and 144 nodal values per direction
+    "landau_dg4_16": Workload("landau_dg4_16", _landau(3, 16, 0.1, 0.5), N.SLDG_INIT_LANDAU,
+                              (0.5, 0.5, 0.5), 500),
+    "landau_dg4_32": Workload("landau_dg4_32", _landau(3, 32, 0.1, 0.5), N.SLDG_INIT_LANDAU,
+                              (0.5, 0.5, 0.5), 500),
+    "landau_dg4_36": Workload("landau_dg4_36", _landau(3, 36, 0.1, 0.5), N.SLDG_INIT_LANDAU,
+                              (0.5, 0.5, 0.5), 500),
+    # the paper's two-stream instability (Sec. 5, Eq. (iv-tsi): eps 1e-3, k 0.2,
+    # v0 2.4 on [0, 10 pi]^2 x [-6, 6]^2), dG4 at 32, 64 and 128 nodal values
+    # per direction, dt 0.1 to T = 250 (quiescent to t ~ 175, growth to ~ 225)
+    **{f"two_stream_paper_dg4_{nc}": Workload(
+        f"two_stream_paper_dg4_{nc}",
+        Config(degree=3, ncell=(nc,) * 4, lo=TSI_PAPER_LO, hi=TSI_PAPER_HI, dt=0.1),
+        N.SLDG_INIT_TWO_STREAM_PAPER, (1e-3, 0.2, 2.4), 2500) for nc in (8, 16, 32)},
     # adjoint of nonlinear Landau damping, 32^4 cells, degree 1, dt 0.1, 100 steps, ckpt 10
     "adjoint_landau_32": Workload("adjoint_landau_32", _landau(1, 32, 0.1, 0.5), N.SLDG_INIT_LANDAU,
                                   (0.5, 0.5, 0.5), 100, ckpt=10),

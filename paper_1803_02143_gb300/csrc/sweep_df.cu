@@ -1,7 +1,7 @@
 // sweep_df.cu -- double-float instantiations of the sweep kernels: FP64
 // storage, arithmetic on the FP32 pipe (the forward sweeps of FP64 contexts).
 // The packed FP32x2 kernels (sweep_df2.cuh for x1, sweep_df3.cuh for the
-// strided directions) take degrees 0..2 on aligned layouts; everything else
+// strided directions) take degrees 0..3 on aligned layouts; everything else
 // runs the one-lane double-float kernels.
 #include "sweep_df2.cuh"
 #include "sweep_df3.cuh"
@@ -9,8 +9,25 @@
 
 namespace sldg {
 
+// degree 3 (the paper's dG4): the warp-per-pair x1 and the strided kernels
+static cudaError_t launch_sweep_df_n4(const SweepArgs& a, cudaStream_t st) {
+  if (a.adjoint || (reinterpret_cast<uintptr_t>(a.f) & 15)) return cudaErrorNotSupported;
+  auto go = [&](auto in_t, auto out_t) -> cudaError_t {
+    constexpr bool I = decltype(in_t)::value, O = decltype(out_t)::value;
+    if (a.dim == 0) return launch_x1_warp_T<4, I, O>(a, st);
+    if (a.inner % 2) return cudaErrorNotSupported;
+    return launch_strided_df3_T<4, I, O>(a, st);
+  };
+  using T = std::true_type;
+  using F = std::false_type;
+  if (a.in_df && a.out_df) return go(T(), T());
+  if (a.in_df) return go(T(), F());
+  if (a.out_df) return go(F(), T());
+  return go(F(), F());
+}
+
 cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st) {
-  const cudaError_t e = launch_sweep_df2(a, st);
+  const cudaError_t e = a.n == 4 ? launch_sweep_df_n4(a, st) : launch_sweep_df2(a, st);
   if (e != cudaErrorNotSupported) return e;
   if (a.in_df && a.out_df) return launch_sweep_any<PolDFT<true, true>>(a, st);
   if (a.in_df) return launch_sweep_any<PolDFT<true, false>>(a, st);
@@ -23,6 +40,7 @@ cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st) {
     case 1: return launch_ebar_df3_T<1>(a, st);
     case 2: return launch_ebar_df3_T<2>(a, st);
     case 3: return launch_ebar_df3_T<3>(a, st);
+    case 4: return launch_ebar_df3_T<4>(a, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -42,6 +60,7 @@ cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const i
     case 1: return go(std::integral_constant<int, 1>());
     case 2: return go(std::integral_constant<int, 2>());
     case 3: return go(std::integral_constant<int, 3>());
+    case 4: return go(std::integral_constant<int, 4>());
     default: return cudaErrorNotSupported;
   }
 }

@@ -483,7 +483,7 @@ __device__ __forceinline__ void x1w_load_cell(const float4* __restrict__ pl, int
 }
 
 template <int N, bool IN_DF, bool OUT_DF>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, N >= 4 ? 2 : 3)
     k_sweep_x1_warp(double* __restrict__ f, int nc, long long npairs, int pairs_per_warp,
                     const float2* __restrict__ ab2, const int* __restrict__ svec, long long mcount,
                     int key_div, int key_mod) {

@@ -19,6 +19,7 @@ cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const 
     case 1: return launch_x12_N<1>(ff, g, ab1, s1, ab2, s2, st);
     case 2: return launch_x12_N<2>(ff, g, ab1, s1, ab2, s2, st);
     case 3: return launch_x12_N<3>(ff, g, ab1, s1, ab2, s2, st);
+    case 4: return launch_x12_N<4>(ff, g, ab1, s1, ab2, s2, st);
     default: return cudaErrorNotSupported;
   }
 }

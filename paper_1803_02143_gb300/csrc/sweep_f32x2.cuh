@@ -234,7 +234,7 @@ cudaError_t launch_strided_f2_T(const SweepArgs& a, cudaStream_t st) {
 constexpr int kF2X1PairsPerWarp = 8;
 
 template <int N>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, N >= 4 ? 3 : 4)
     k_sweep_x1_f2warp(float* __restrict__ f, int nc, long long npairs, int pairs_per_warp,
                       const float* __restrict__ ab, const int* __restrict__ svec,
                       long long mcount, int key_div, int key_mod) {
@@ -348,13 +348,14 @@ cudaError_t launch_sweep_f2_N(const SweepArgs& a, cudaStream_t st) {
   return a.dim == 0 ? launch_x1_f2warp_T<N>(a, st) : launch_strided_f2_T<N>(a, st);
 }
 
-// Packed FP32 forward sweeps for degrees 0..2 on aligned layouts;
+// Packed FP32 forward sweeps for degrees 0..3 on aligned layouts;
 // cudaErrorNotSupported sends the caller to the one-lane kernels.
 inline cudaError_t launch_sweep_f2(const SweepArgs& a, cudaStream_t st) {
   switch (a.n) {
     case 1: return launch_sweep_f2_N<1>(a, st);
     case 2: return launch_sweep_f2_N<2>(a, st);
     case 3: return launch_sweep_f2_N<3>(a, st);
+    case 4: return launch_sweep_f2_N<4>(a, st);
     default: return cudaErrorNotSupported;
   }
 }

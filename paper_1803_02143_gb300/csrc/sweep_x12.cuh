@@ -46,7 +46,7 @@ __device__ __forceinline__ float2 ld_cluster_f2(unsigned addr) {
 
 // CPL: cells of an x1 line per lane (nc0 <= 32 CPL)
 template <int N, int CPL>
-__global__ void __launch_bounds__(kX12Threads, 3)
+__global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     k_sweep_x12_f32(float* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
                     const float* __restrict__ ab2, const int* __restrict__ s2) {

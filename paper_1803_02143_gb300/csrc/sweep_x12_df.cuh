@@ -25,7 +25,7 @@ __device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
 }
 
 template <int N, int CPL, bool IN_DF, bool OUT_DF>
-__global__ void __launch_bounds__(kX12Threads, 3)
+__global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
     k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
                    const float2* __restrict__ ab1, const int* __restrict__ s1,
                    const float2* __restrict__ ab2, const int* __restrict__ s2) {

@@ -1,8 +1,9 @@
 """Parity at full size, in the launch configuration bench.py times: the
 bench workload (nonlinear Landau damping, 64^4 cells, degree 2, 1.36e9 nodal
 values), the two-stream workload (64^2 x 128^2 cells, degree 2, 5.4e9 values)
-and the large mixed-precision workload (128^4 cells, degree 1, 4.3e9 values,
-FP32 storage).
+the large mixed-precision workload (128^4 cells, degree 1, 4.3e9 values,
+FP32 storage) and the paper's dG4 Landau run (36^4 cells, degree 3, 4.3e8
+values).
 
 The oracle cannot step 1.36e9 values, so each stage of the Strang step is
 run alone through the C ABI (the same kernels sldg_step launches) and
@@ -25,7 +26,7 @@ NLINES = 48
 
 CASES = [("nonlinear_landau_64", "fp64"), ("nonlinear_landau_64", "fp32"),
          ("two_stream_64x128", "fp64"), ("two_stream_64x128", "fp32"),
-         ("mixed_landau_128", "fp32")]
+         ("mixed_landau_128", "fp32"), ("landau_dg4_36", "fp64"), ("landau_dg4_36", "fp32")]
 
 
 @pytest.fixture(scope="module")

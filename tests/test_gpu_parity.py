@@ -58,7 +58,9 @@ GRIDS = [
     (2, (13, 11, 12, 9)),  # D = 39, 33, 36, 27: several tiles, ragged tails
     (3, (4, 6, 5, 7)),
     (0, (9, 8, 10, 7)),
+    (3, (9, 8, 6, 5)),     # dG4: D = 36, 32, 24, 20, x1 lines past one lane tile
 ]
+GRIDS32 = GRIDS[:3] + GRIDS[4:]
 
 
 @pytest.mark.parametrize("deg,nc", GRIDS)
@@ -83,7 +85,7 @@ def test_sweep_fp64(lib, orc, deg, nc, dim, vbc, flags):
     s.close()
 
 
-@pytest.mark.parametrize("deg,nc", GRIDS[:2])
+@pytest.mark.parametrize("deg,nc", GRIDS32)
 @pytest.mark.parametrize("dim", [0, 1, 2, 3])
 def test_sweep_fp32(lib, orc, deg, nc, dim):
     s, og = make(lib, orc, deg, nc, dt=0.37, prec="fp32")
@@ -322,7 +324,7 @@ def test_host_batches_match_single_steps(lib, orc, prec):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("deg,nc", [(2, (8, 8, 6, 5)), (1, (16, 12, 7, 6)), (2, (12, 16, 5, 4)),
-                                    (0, (36, 10, 9, 8))])
+                                    (0, (36, 10, 9, 8)), (3, (9, 8, 6, 5))])
 def test_fused_x_pass_matches_separate_sweeps(lib, orc, deg, nc, prec):
     # one fused X1 X2 pass (thread-block clusters) gives the bits of the two
     # separate sweeps (the same arithmetic on the same values); both stay

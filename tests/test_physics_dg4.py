@@ -1,0 +1,150 @@
+"""The paper's own dG4 (degree 3) runs on the GPU, checked against physics
+that does not come from the oracle.
+
+- Two-stream instability, Eq. (iv-tsi) as printed (Sec. 5: eps 1e-3, k 0.2,
+  v0 2.4, [0, 10 pi]^2 x [-6, 6]^2, dt 0.1), at the paper's smallest dG4
+  resolution (32 nodal values per direction).  The perturbation
+  cos(k x1) cos(k x2) seeds the wave vectors (+-k, +-k).  Along
+  u = (v1 + v2)/sqrt(2) the four Maxwellians of f_eq project onto three
+  (weights 1/4, 1/2, 1/4 at -sqrt(2) v0, 0, sqrt(2) v0), and the linear
+  dispersion relation of that distribution at |k| = 0.2 sqrt(2) has an
+  unstable root omega_r + i gamma.  In the linear phase the field energy
+  oscillates at 2 omega_r and grows as exp(2 gamma t): the peaks of ln W
+  give both.
+- Nonlinear Landau damping at the paper's Sec. 4 resolution (144 nodal
+  values per direction, dt 0.1, T = 50): mass and total energy after 500
+  steps.
+
+The dispersion roots come from the plasma dispersion function; the CPU tests
+pin that routine against the textbook Landau root and against direct
+quadrature of the dielectric function.
+"""
+import numpy as np
+import pytest
+
+from conftest import golden_kv
+
+torch = pytest.importorskip("torch")
+
+
+def dielectric(om, k, beams):
+    """1 + sum_j w_j k^-2 (1 + zeta_j Z(zeta_j)), zeta_j = (om/k - c_j)/sqrt(2):
+    unit-variance Maxwellians of weight w_j drifting at c_j, unit plasma
+    frequency, Z(z) = i sqrt(pi) w(z) (the Faddeeva function)."""
+    from scipy.special import wofz
+
+    r = 1.0 + 0j
+    for c, w in beams:
+        z = (om / k - c) / np.sqrt(2)
+        r += w / k ** 2 * (1 + z * 1j * np.sqrt(np.pi) * wofz(z))
+    return r
+
+
+def root(k, beams, guess):
+    from scipy.optimize import fsolve
+
+    def F(x):
+        d = dielectric(x[0] + 1j * x[1], k, beams)
+        return [d.real, d.imag]
+
+    x = fsolve(F, guess, xtol=1e-12)
+    return x[0], x[1]
+
+
+def tsi_kk_beams(v0):
+    u = np.sqrt(2) * v0
+    return [(u, 0.25), (0.0, 0.5), (-u, 0.25)]
+
+
+def test_dispersion_routine_textbook_landau_root():
+    ref = golden_kv("landau_dispersion_k05.txt")
+    om, ga = root(ref["k"], [(0.0, 1.0)], [1.4, -0.15])
+    assert abs(om - ref["omega_r"]) < ref["abs_tol"] and abs(ga - ref["gamma"]) < ref["abs_tol"]
+
+
+def test_dispersion_growing_root_matches_quadrature():
+    # for Im(omega) > 0 the dielectric function is the plain real-line integral
+    # 1 - k^-2 int F'(u) / (u - omega/k) du; evaluate it at the root by quadrature
+    from scipy.integrate import quad
+
+    k, beams = 0.2 * np.sqrt(2), tsi_kk_beams(2.4)
+    om, ga = root(k, beams, [0.6, 0.07])
+    assert ga > 0.01
+    p = (om + 1j * ga) / k
+
+    def dF(u):
+        return sum(-w * (u - c) * np.exp(-(u - c) ** 2 / 2) / np.sqrt(2 * np.pi) for c, w in beams)
+
+    re = quad(lambda u: (dF(u) / (u - p)).real, -30, 30, limit=400, points=[om / k])[0]
+    im = quad(lambda u: (dF(u) / (u - p)).imag, -30, 30, limit=400, points=[om / k])[0]
+    eps = 1 - (re + 1j * im) / k ** 2
+    assert abs(eps) < 1e-8, eps
+    # the symmetric two-beam root is purely growing
+    om2, ga2 = root(0.2, [(2.4, 0.5), (-2.4, 0.5)], [0.0, 0.2])
+    assert abs(om2) < 1e-10 and ga2 > 0.1
+    assert abs(dielectric(om2 + 1j * ga2, 0.2, [(2.4, 0.5), (-2.4, 0.5)])) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_02143_gb300 import build
+
+    build.build()
+    import paper_1803_02143_gb300 as P
+
+    return P
+
+
+def _peaks(W, dt, t0, t1):
+    lw = np.log(W)
+    t = np.arange(1, len(W) + 1) * dt
+    tp, lp = [], []
+    for i in range(1, len(W) - 1):
+        if lw[i] > lw[i - 1] and lw[i] > lw[i + 1] and t0 <= t[i] <= t1:
+            a, b, c = lw[i - 1], lw[i], lw[i + 1]
+            d = 0.5 * (a - c) / (a - 2 * b + c)
+            tp.append(t[i] + d * dt)
+            lp.append(b - 0.25 * (a - c) * d)
+    return np.array(tp), np.array(lp)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_two_stream_linear_growth(lib, prec):
+    from paper_1803_02143_gb300 import configs
+
+    w = configs.workload("two_stream_paper_dg4_8", prec)
+    eps, k, v0 = w.params
+    om, ga = root(k * np.sqrt(2), tsi_kk_beams(v0), [0.6, 0.07])
+    with lib.Sldg(w.cfg) as s:
+        s.set_initial(w.kind, w.params)
+        W = s.step(600, history=True)
+    # linear phase: after the damped components have decayed, before the
+    # second-order modes catch up
+    tp, lp = _peaks(W, w.cfg.dt, 25.0, 50.0)
+    assert len(tp) >= 4
+    g = np.polyfit(tp, lp, 1)[0] / 2
+    o = np.pi / np.mean(np.diff(tp))
+    assert abs(g - ga) < 0.03 * ga, (g, ga)
+    assert abs(o - om) < 0.02 * om, (o, om)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_landau_dg4_mass_and_energy(lib, prec):
+    from paper_1803_02143_gb300 import configs
+
+    w = configs.workload("landau_dg4_36", prec)
+    with lib.Sldg(w.cfg) as s:
+        s.set_initial(w.kind, w.params)
+        d0 = s.diagnostics()
+        s.step(w.steps)
+        d1 = s.diagnostics()
+    assert abs(d1["t"] - 50.0) < 1e-9
+    # outflow through v = +-6 is below 1e-7 of the mass for this Maxwellian;
+    # FP32 storage rounds every sweep output
+    assert abs(d1["mass"] - d0["mass"]) < (1e-6 if prec == "fp64" else 1e-4) * d0["mass"]
+    # Sec. 4: the energy error of the dG4 scheme at dt 0.1 is of order 1e-3
+    assert abs(d1["total"] - d0["total"]) < 2e-3 * d0["total"]
