@@ -44,8 +44,18 @@ __device__ __forceinline__ float2 ld_cluster_f2(unsigned addr) {
   return v;
 }
 
-// CPL: cells of an x1 line per lane (nc0 <= 32 CPL)
-template <int N, int CPL>
+// Lanes given to one row pair in the X1 phase: the smallest power of two
+// covering the line at cpl cells per lane (at most 32).
+__host__ __device__ __forceinline__ int x12_lanes_per_pair(int nc0, int cpl) {
+  const int need = (nc0 + cpl - 1) / cpl;
+  int l = 1;
+  while (l < need && l < 32) l *= 2;
+  return l;
+}
+
+// CPL: cells of an x1 line per lane (nc0 <= 32 CPL); GRP: several lane
+// groups per warp in the X1 phase (lines of at most 16 CPL cells)
+template <int N, int CPL, bool GRP>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     k_sweep_x12_f32(float* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
@@ -71,7 +81,9 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
   __syncthreads();
 
-  // 2. X1 in place, warp per row pair (the two lanes of every FP32x2 op)
+  // 2. X1 in place, a group of lpp lanes per row pair (the two lanes of every
+  //    FP32x2 op are the pair's two rows); short lines put several groups in
+  //    one warp
   {
     float2 A[NN], B[NN];
 #pragma unroll
@@ -81,8 +93,11 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       B[i] = make_float2(b, b);
     }
     const int sa = wrap_cell(-s1[key1] - 1, nc0);
-    const int cb = min(lane * CPL, nc0), ce = min(cb + CPL, nc0);
-    for (int p = wid; p < H / 2; p += nw) {
+    const int lpp = GRP ? x12_lanes_per_pair(nc0, CPL) : 32, G = GRP ? 32 / lpp : 1;
+    const int grp = GRP ? lane / lpp : 0, gl = lane - grp * lpp;
+    const unsigned gmask = GRP ? ((1u << lpp) - 1) << (grp * lpp) : 0xffffffffu;
+    const int cb = min(gl * CPL, nc0), ce = min(cb + CPL, nc0);
+    for (int p = wid * G + grp; p < H / 2; p += nw * G) {
       float* ra = rows + (2 * p) * D0;
       float* rb = ra + D0;
       float2 x[CPL + 1][N];
@@ -96,7 +111,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
         }
         k = k + 1 == nc0 ? 0 : k + 1;
       }
-      __syncwarp();
+      __syncwarp(gmask);
 #pragma unroll
       for (int t = 0; t < CPL; ++t) {
         const int c = cb + t;
@@ -110,7 +125,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
           }
         }
       }
-      __syncwarp();
+      __syncwarp(gmask);
     }
   }
   // 3. every CTA's rows hold X1 f
@@ -178,9 +193,10 @@ cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1
   const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 4 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
-  // the smallest cluster whose row share fits three CTAs per SM
+  // the smallest cluster (a single CTA when the plane fits) whose row share
+  // fits three CTAs per SM
   int cs = 0;
-  for (int c = 2; c <= 8; c *= 2) {
+  for (int c = 1; c <= 8; c *= 2) {
     if (nc1 % c) continue;
     const long long H = (long long)(nc1 / c) * N;
     if (H % 2 || (H * D0) % 4) continue;
@@ -191,7 +207,8 @@ cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1
   }
   if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
   const size_t smem = (size_t)(nc1 / cs) * N * D0 * sizeof(float);
-  auto kfn = k_sweep_x12_f32<N, CPL>;
+  auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_f32<N, CPL, true>
+                                               : k_sweep_x12_f32<N, CPL, false>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

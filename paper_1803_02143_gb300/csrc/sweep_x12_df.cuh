@@ -24,7 +24,7 @@ __device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
   return v;
 }
 
-template <int N, int CPL, bool IN_DF, bool OUT_DF>
+template <int N, int CPL, bool GRP, bool IN_DF, bool OUT_DF>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
     k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
                    const float2* __restrict__ ab1, const int* __restrict__ s1,
@@ -56,11 +56,15 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
   cp_async_wait_all();
   __syncthreads();
 
-  // X1 in place, warp per row pair; outputs as column pairs
+  // X1 in place, a lane group per row pair (several groups per warp on short
+  // lines); outputs as column pairs
   {
     const int sa = wrap_cell(-s1[key1] - 1, nc0);
-    const int cb = min(lane * CPL, nc0), ce = min(cb + CPL, nc0);
-    for (int p = wid; p < H / 2; p += nw) {
+    const int lpp = GRP ? x12_lanes_per_pair(nc0, CPL) : 32, G = GRP ? 32 / lpp : 1;
+    const int grp = GRP ? lane / lpp : 0, gl = lane - grp * lpp;
+    const unsigned gmask = GRP ? ((1u << lpp) - 1) << (grp * lpp) : 0xffffffffu;
+    const int cb = min(gl * CPL, nc0), ce = min(cb + CPL, nc0);
+    for (int p = wid * G + grp; p < H / 2; p += nw * G) {
       double* ra = rows + (2 * p) * D0;
       double* rb = ra + D0;
       float2 xh[CPL + 1][N], xl[CPL + 1][N];
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
         }
         k = k + 1 == nc0 ? 0 : k + 1;
       }
-      __syncwarp();
+      __syncwarp(gmask);
       float* fa = reinterpret_cast<float*>(ra);
       float* fb = reinterpret_cast<float*>(rb);
 #pragma unroll
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
           }
         }
       }
-      __syncwarp();
+      __syncwarp(gmask);
     }
   }
   cluster_sync();
@@ -177,7 +181,8 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
   }
   if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
   const size_t smem = mats + (size_t)(nc1 / cs) * N * D0 * sizeof(double);
-  auto kfn = k_sweep_x12_df<N, CPL, IN_DF, OUT_DF>;
+  auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_df<N, CPL, true, IN_DF, OUT_DF>
+                                               : k_sweep_x12_df<N, CPL, false, IN_DF, OUT_DF>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
