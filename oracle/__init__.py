@@ -18,7 +18,9 @@ reproduction, mass conservation and the two-cell stencil; the Poisson map
 against closed-form fields; the full step against the free-streaming closed
 form, the convergence order l+1 and the linear Landau damping rate from the
 dispersion relation; the adjoint against dot-product identities and central
-finite differences.
+finite differences; the splitting compositions (order 4, merged drifts)
+against the tabulated triple-jump weights, the convergence orders of an
+exactly split pendulum, free streaming and linear Landau damping.
 """
 from __future__ import annotations
 
@@ -67,6 +69,7 @@ class _CGrid(ctypes.Structure):
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
 
 
 def _lib_handle():
@@ -100,6 +103,10 @@ def _lib_handle():
             "orc_init": (ctypes.c_int, [G, ctypes.c_int, _DP, _DP]),
             "orc_step": (ctypes.c_int, [G, _DP, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP]),
             "orc_fields_of": (ctypes.c_int, [G, _DP, _DP, _DP, _DP]),
+            "orc_split_stages": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP,
+                                                _DP, ctypes.c_int]),
+            "orc_step_split": (ctypes.c_int, [G, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _DP, _DP, _DP]),
             "orc_backward": (ctypes.c_int, [G, _DP, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP,
                                             _DP]),
             "orc_threads": (ctypes.c_int, []),
@@ -331,6 +338,34 @@ def step(g: Grid, f, nsteps: int = 1, kick: bool = True):
     rc = _lib_handle().orc_step(g.c(), _p(f), int(nsteps), int(kick), _p(W), _p(E1), _p(E2))
     if rc != 0:
         raise MemoryError("orc_step failed")
+    return f, W[:nsteps], E1, E2
+
+
+def split_stages(order: int, nsteps: int, merge: bool = False):
+    """The stage list of nsteps steps of the splitting of the given order:
+    (kinds, fracs), kind 0 = drift, 1 = kick, 2 = first kick of a step."""
+    cap = 9 * nsteps + 2
+    kind = np.zeros(cap, dtype=np.int32)
+    frac = np.zeros(cap)
+    n = _lib_handle().orc_split_stages(int(order), int(nsteps), int(bool(merge)),
+                                       kind.ctypes.data_as(_IP), _p(frac), cap)
+    if n < 0:
+        raise ValueError("unsupported splitting order")
+    return kind[:n].copy(), frac[:n].copy()
+
+
+def step_split(g: Grid, f, nsteps: int = 1, order: int = 2, merge: bool = False,
+               kick: bool = True):
+    """Advance a copy of f by nsteps steps of the order-2 or order-4 splitting,
+    optionally with merged drifts. Returns (f, W_hist, E1, E2)."""
+    f = np.array(_f(g, f), copy=True)
+    W = np.zeros(max(nsteps, 1))
+    E1 = np.zeros(g.xshape)
+    E2 = np.zeros(g.xshape)
+    rc = _lib_handle().orc_step_split(g.c(), _p(f), int(nsteps), int(order), int(bool(merge)),
+                                      int(kick), _p(W), _p(E1), _p(E2))
+    if rc != 0:
+        raise ValueError("orc_step_split failed")
     return f, W[:nsteps], E1, E2
 
 

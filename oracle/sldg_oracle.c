@@ -758,6 +758,107 @@ int orc_step(const orc_grid* g, double* f, int nsteps, int kick, double* W_hist,
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Splitting compositions built on the Strang step (Sec. 2 cites higher     */
+/* order splittings).  order 2: the Strang step itself.  order 4: the       */
+/* symmetric triple jump S(g1 tau) S(g0 tau) S(g1 tau) of Strang steps,     */
+/* g1 = 1 / (2 - 2^(1/3)), g0 = 1 - 2 g1 (g0 < 0): the weights with         */
+/* 2 g1 + g0 = 1 and 2 g1^3 + g0^3 = 0, which cancel the tau^3 error of a   */
+/* symmetric second-order step.                                             */
+/* Stage list of nsteps steps: kind 0 = drift e^{frac tau A} (x1 then x2),  */
+/* 1 = kick e^{frac tau B} (field from the current rho, v1 then v2), 2 = the */
+/* first kick of a step (its W is recorded).  merge: consecutive drifts     */
+/* (across sub-steps and steps) become one drift of the summed fraction,    */
+/* which equals the separate drifts for the exact flow but not after the    */
+/* SLDG projection.  Returns the number of stages, -1 if cap is too small   */
+/* or the order is not 2 or 4.                                              */
+/* ------------------------------------------------------------------------ */
+static int push_stage(int* kind, double* frac, int* n, int cap, int k, double fr) {
+  if (*n >= cap) return -1;
+  kind[*n] = k;
+  frac[*n] = fr;
+  ++*n;
+  return 0;
+}
+
+int orc_split_stages(int order, int nsteps, int merge, int* kind, double* frac, int cap) {
+  double gam[3];
+  int ns;
+  if (order == 2) {
+    gam[0] = 1.0;
+    ns = 1;
+  } else if (order == 4) {
+    gam[0] = 1.0 / (2.0 - cbrt(2.0));
+    gam[1] = 1.0 - 2.0 * gam[0];
+    gam[2] = gam[0];
+    ns = 3;
+  } else {
+    return -1;
+  }
+  int n = 0;
+  double pending = 0.0; /* merge: the drift carried over from the last kick */
+  for (int m = 0; m < nsteps; ++m)
+    for (int i = 0; i < ns; ++i) {
+      const double a = 0.5 * gam[i];
+      if (push_stage(kind, frac, &n, cap, 0, merge ? pending + a : a)) return -1;
+      if (push_stage(kind, frac, &n, cap, i == 0 ? 2 : 1, gam[i])) return -1;
+      if (merge)
+        pending = a;
+      else if (push_stage(kind, frac, &n, cap, 0, a))
+        return -1;
+    }
+  if (merge && nsteps > 0 && push_stage(kind, frac, &n, cap, 0, pending)) return -1;
+  return n;
+}
+
+/* nsteps steps of the composition (order, merge) of orc_split_stages; the
+ * arguments and outputs as orc_step (W_hist[m]: W at the first kick of step
+ * m). */
+int orc_step_split(const orc_grid* g, double* f, int nsteps, int order, int merge, int kick,
+                   double* W_hist, double* E1, double* E2) {
+  const int cap = 9 * nsteps + 2;
+  int* kind = (int*)malloc((size_t)cap * sizeof(int));
+  double* fr = (double*)malloc((size_t)cap * sizeof(double));
+  long N = orc_numel(g), Dx = dimlen(g, 0) * dimlen(g, 1);
+  double* tmp = (double*)malloc((size_t)N * sizeof(double));
+  orc_fields fl;
+  fl.rho = (double*)malloc((size_t)Dx * sizeof(double));
+  fl.E1 = (double*)calloc((size_t)Dx, sizeof(double));
+  fl.E2 = (double*)calloc((size_t)Dx, sizeof(double));
+  if (!kind || !fr || !tmp || !fl.rho || !fl.E1 || !fl.E2) return -3;
+  const int n = orc_split_stages(order, nsteps, merge, kind, fr, cap);
+  if (n < 0) return -1;
+  int m = 0;
+  for (int q = 0; q < n; ++q) {
+    if (kind[q] == 0) {
+      orc_sweep(g, 0, NULL, fr[q], f, tmp);
+      orc_sweep(g, 1, NULL, fr[q], tmp, f);
+      continue;
+    }
+    if (kick) {
+      orc_rho(g, f, fl.rho);
+      orc_poisson(g, fl.rho, fl.E1, fl.E2);
+    } else {
+      for (long p = 0; p < Dx; ++p) fl.E1[p] = fl.E2[p] = 0.0;
+    }
+    if (kind[q] == 2) {
+      if (W_hist) W_hist[m] = orc_electric_energy(g, fl.E1, fl.E2);
+      ++m;
+    }
+    orc_sweep(g, 2, fl.E1, fr[q], f, tmp);
+    orc_sweep(g, 3, fl.E2, fr[q], tmp, f);
+  }
+  if (E1) memcpy(E1, fl.E1, (size_t)Dx * sizeof(double));
+  if (E2) memcpy(E2, fl.E2, (size_t)Dx * sizeof(double));
+  free(kind);
+  free(fr);
+  free(tmp);
+  free(fl.rho);
+  free(fl.E1);
+  free(fl.E2);
+  return 0;
+}
+
 /* rho and E of the current f (no sweep). */
 int orc_fields_of(const orc_grid* g, const double* f, double* rho, double* E1, double* E2) {
   orc_rho(g, f, rho);
