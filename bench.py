@@ -329,6 +329,28 @@ def run_forward(w, steps, warmup, world, local, sample_clocks=True):
     return s, ms, timing, launches, ck
 
 
+def run_splitting_variants(args, w, flags, local):
+    """Step time of the same workload and precision with merged drifts (one x
+    pass per step instead of two) and with the order-4 triple jump (three
+    Strang sub-steps per step), merged or not."""
+    from paper_1803_02143_gb300 import _native as N
+    from paper_1803_02143_gb300 import configs
+
+    out = {}
+    for name, fl in (("strang_merged", N.SLDG_FLAG_MERGE_DRIFTS), ("order4", N.SLDG_FLAG_ORDER4),
+                     ("order4_merged", N.SLDG_FLAG_ORDER4 | N.SLDG_FLAG_MERGE_DRIFTS)):
+        w3 = configs.workload(args.workload, w.cfg.precision, flags | fl)
+        s3, ms3, _, _, _ = run_forward(w3, args.steps, args.warmup, 1, local, sample_clocks=False)
+        s3.close()
+        del s3
+        import torch
+
+        torch.cuda.empty_cache()
+        out[name] = {"ms_per_step": ms3 / args.steps,
+                     "value": w3.cfg.numel * args.steps / (ms3 / 1e3), "unit": UNIT}
+    return out
+
+
 def run_e2e(s, w, steps):
     """Through the C ABI with host buffers: every step uploads its input
     state from pinned host memory and reads its W back
@@ -437,6 +459,7 @@ def run_ours(args, world, rank, local):
         elif "fp64" in times:
             extras["fp32_over_fp64_step_time"] = ms / times["fp64"]
         extras["adjoint"] = run_adjoint_ratio()
+        extras["splitting"] = run_splitting_variants(args, w, flags, local)
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle as orc

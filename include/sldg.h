@@ -67,6 +67,22 @@ extern "C" {
                                    instead of one fused pass over each x-plane
                                    (FP32: the same bits; FP64 double-float: the
                                    same arithmetic to its rounding) */
+#define SLDG_FLAG_ORDER4 4      /* sldg_step: every step is the fourth-order
+                                   triple jump S(w1 tau) S(w0 tau) S(w1 tau) of
+                                   Strang steps S, w1 = 1/(2 - 2^(1/3)),
+                                   w0 = 1 - 2 w1 < 0 (Sec. 2 cites higher-order
+                                   splittings; these are Yoshida's weights);
+                                   W_history[m] is W at the first kick of step m */
+#define SLDG_FLAG_MERGE_DRIFTS 8 /* sldg_step: consecutive x drifts within one
+                                   call (the last drift of a step and the first of
+                                   the next, and between ORDER4 sub-steps) run as
+                                   one drift of the summed fraction: fewer passes
+                                   over f, but not the result of the separate
+                                   drifts (the SLDG projection does not compose
+                                   exactly), so steps of different calls differ
+                                   from one call of all the steps */
+/* sldg_record and sldg_backward differentiate the Strang step: with ORDER4
+ * or MERGE_DRIFTS they return SLDG_ERR_UNSUPPORTED. */
 
 #define SLDG_VBC_ZERO_INFLOW 0 /* v-sweeps drop source cells outside the box */
 #define SLDG_VBC_PERIODIC 1    /* v-sweeps wrap (test mode: exact mass) */
@@ -128,7 +144,7 @@ int sldg_abi_version(void);
  * nodes, the x-sweep matrices (one pair per v-node, Sec. 3: "precomputed") and
  * the spectral tables.  f_dev is not read or written here.
  * Errors: BAD_CONFIG (degree outside 0..3, ncell < 2, hi <= lo, dt <= 0,
- * unknown precision/vbc, flags != 0, a line too long for on-chip staging),
+ * unknown precision/vbc, unknown flag bits, a line too long for on-chip staging),
  * BAD_PTR (cfg or out NULL, f_dev NULL or misaligned), OOM, CUDA. */
 int sldg_init(const sldg_config* cfg, void* f_dev, void* stream, sldg_ctx** out);
 
@@ -160,9 +176,11 @@ int sldg_set_f(sldg_ctx* ctx, const void* src, int on_device, double t, long lon
  * sldg_step: advance f in place by nsteps Strang steps (Sec. 2):
  *   X1(tau/2) X2(tau/2) | rho = Q f, E = L rho | V1(tau E1) V2(tau E2) | X1(tau/2) X2(tau/2)
  * with E frozen over the kick (Sec. 2: the acceleration leaves rho
- * invariant).  If W_history (host, nsteps doubles) is non-NULL it receives
- * the electric energy W(E) of each step's kick field and the call
- * synchronises the stream; otherwise the call is asynchronous.
+ * invariant); with SLDG_FLAG_ORDER4 / SLDG_FLAG_MERGE_DRIFTS the
+ * compositions those flags describe.  If W_history (host, nsteps doubles)
+ * is non-NULL it receives the electric energy W(E) of each step's (first)
+ * kick field and the call synchronises the stream; otherwise the call is
+ * asynchronous.
  * Errors: ARG (nsteps < 0), CUDA. */
 int sldg_step(sldg_ctx* ctx, int nsteps, double* W_history);
 
@@ -223,7 +241,8 @@ int sldg_sweep_adjoint(sldg_ctx* ctx, int dim, double frac, void* lam, const voi
  * checkpoint of f every ckpt_every steps in a library-owned device pool
  * (ceil(nsteps / ckpt_every) copies of f), and record W of each step
  * (W_history, host, nullable).  Prepares sldg_backward.
- * Errors: ARG, OOM (the pool does not fit), CUDA. */
+ * Errors: ARG, OOM (the pool does not fit), UNSUPPORTED (SLDG_FLAG_ORDER4 or
+ * SLDG_FLAG_MERGE_DRIFTS), CUDA. */
 int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
 
 /* Reverse pass of the last sldg_record: gradient of
@@ -243,7 +262,8 @@ int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
  * log2(ckpt_every) times; with one slot, from the checkpoint for every
  * step.  The gradient is the same whatever the number of slots (the same
  * arithmetic, only repeated).
- * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits), CUDA. */
+ * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits),
+ * UNSUPPORTED (SLDG_FLAG_ORDER4 or SLDG_FLAG_MERGE_DRIFTS), CUDA. */
 int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
 
 /* Upper bound on the recomputation slots of sldg_backward (0 = as many as a

@@ -145,7 +145,9 @@ int validate(const sldg_config* cfg) {
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
   if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
   if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION)) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION | SLDG_FLAG_ORDER4 |
+                     SLDG_FLAG_MERGE_DRIFTS))
+    return SLDG_ERR_BAD_CONFIG;
   return SLDG_OK;
 }
 
@@ -166,11 +168,13 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_wv);
   dfree(c->d_wv2);
   dfree(c->d_wx);
+  auto free_set = [](MatSet* m) {
+    dfree(m->ab); dfree(m->dab); dfree(m->dab2); dfree(m->ab2); dfree(m->s);
+    dfree(m->abt); dfree(m->abt2); dfree(m->st);
+  };
   for (int d = 0; d < 2; ++d) {
-    for (MatSet* m : {&c->xm[d], &c->vm[d]}) {
-      dfree(m->ab); dfree(m->dab); dfree(m->dab2); dfree(m->ab2); dfree(m->s);
-      dfree(m->abt); dfree(m->abt2); dfree(m->st);
-    }
+    for (int k = 0; k < sldg_ctx::kXSlots; ++k) free_set(&c->xm[d][k]);
+    free_set(&c->vm[d]);
     dfree(c->d_E[d]);
     dfree(c->d_Eb[d]);
   }
@@ -234,11 +238,38 @@ int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv, bool trans
   return SLDG_OK;
 }
 
-// x-sweep d (0 or 1): one matrix pair per node of v_{d+1}, shift v dt frac;
-// trans: also the transposed tables of the adjoint
-int ensure_xmats(sldg_ctx* c, int d, double frac, bool trans = false) {
-  MatSet& m = c->xm[d];
-  if (m.valid && m.frac == frac && (!trans || m.with_t)) return SLDG_OK;
+void drop_step_graphs(sldg_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
+    c->step_graph[i] = nullptr;
+  }
+}
+
+// x-sweep d (0 or 1): one matrix pair per node of v_{d+1}, shift v dt frac,
+// in one of a few slots per direction (one per shift fraction in use); trans:
+// also the transposed tables of the adjoint.  Reusing a slot for another
+// fraction drops the recorded step graphs, which read the slots' matrices.
+int ensure_xmats(sldg_ctx* c, int d, double frac, bool trans, MatSet** out) {
+  MatSet* slots = c->xm[d];
+  int k = -1;
+  for (int i = 0; i < sldg_ctx::kXSlots && k < 0; ++i)
+    if (slots[i].valid && slots[i].frac == frac) k = i;
+  if (k >= 0 && (!trans || slots[k].with_t)) {
+    *out = &slots[k];
+    return SLDG_OK;
+  }
+  if (k < 0) {
+    for (int i = 0; i < sldg_ctx::kXSlots && k < 0; ++i)
+      if (!slots[i].valid) k = i;
+    if (k < 0) {
+      k = c->xm_next[d];
+      c->xm_next[d] = (k + 1) % sldg_ctx::kXSlots;
+      drop_step_graphs(c);
+    }
+  }
+  MatSet& m = slots[k];
+  m.valid = false;
+  *out = &m;
   const int vd = d + 2;
   SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false, trans));
   KTimer t(c, SLDG_K_VMAT);
@@ -294,8 +325,7 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   const bool tform = adjoint && (!ebar || ebar_df) && !(c->prec == SLDG_FP64 && native);
   MatSet* m;
   if (dim < 2) {
-    SLDG_TRY(ensure_xmats(c, dim, frac, tform));
-    m = &c->xm[dim];
+    SLDG_TRY(ensure_xmats(c, dim, frac, tform, &m));
     a.periodic = 1;
   } else {
     SLDG_TRY(ensure_vmats(c, dim - 2, frac, ebar, tform));
@@ -398,26 +428,21 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
   return SLDG_OK;
 }
 
-// One Strang step in place on buf; W(E) of the kick field to Wslot (device) if given.
-// FP64 storage with double-float sweeps: buf holds IEEE doubles before and
-// after the step; the five intermediate sub-step states in between are kept
-// as double-float (hi, lo) pairs in the same 8-byte elements, so the
-// conversion to and from the FP32 pipe's format happens once per step.
-// X1(tau/2) X2(tau/2) as one fused pass over each x-plane (FP32 storage,
+// X1(frac tau) X2(frac tau) as one fused pass over each x-plane (FP32 storage,
 // or FP64 storage in double-float arithmetic); *done stays false when the
 // layout does not suit it and the two sweeps must run separately.
-int run_x12(sldg_ctx* c, void* buf, bool in_df, bool out_df, bool* done) {
+int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done) {
   *done = false;
   if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64)) return SLDG_OK;
-  SLDG_TRY(ensure_xmats(c, 0, 0.5));
-  SLDG_TRY(ensure_xmats(c, 1, 0.5));
+  MatSet *m0, *m1;
+  SLDG_TRY(ensure_xmats(c, 0, frac, false, &m0));
+  SLDG_TRY(ensure_xmats(c, 1, frac, false, &m1));
   KTimer t(c, SLDG_K_X12);
   const cudaError_t e =
       c->prec == SLDG_FP32
-          ? launch_sweep_x12_f32(buf, c->g, c->xm[0].ab, c->xm[0].s, c->xm[1].ab, c->xm[1].s,
-                                 c->stream)
-          : launch_sweep_x12_df(buf, c->g, c->xm[0].ab2, c->xm[0].s, c->xm[1].ab2, c->xm[1].s,
-                                in_df ? 1 : 0, out_df ? 1 : 0, c->stream);
+          ? launch_sweep_x12_f32(buf, c->g, m0->ab, m0->s, m1->ab, m1->s, c->stream)
+          : launch_sweep_x12_df(buf, c->g, m0->ab2, m0->s, m1->ab2, m1->s, in_df ? 1 : 0,
+                                out_df ? 1 : 0, c->stream);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -430,26 +455,123 @@ int run_x12(sldg_ctx* c, void* buf, bool in_df, bool out_df, bool* done) {
   return SLDG_OK;
 }
 
-int do_step(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter = nullptr) {
-  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+// X1(frac tau) X2(frac tau): the fused pass, or the two sweeps
+int drift(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df) {
+  const bool df = in_df || out_df;
   bool fused = false;
-  SLDG_TRY(run_x12(c, buf, false, df, &fused));
+  SLDG_TRY(run_x12(c, buf, frac, in_df, out_df, &fused));
   if (!fused) {
-    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
-    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
+    SLDG_TRY(run_sweep(c, buf, 0, frac, false, nullptr, nullptr, in_df, df));
+    SLDG_TRY(run_sweep(c, buf, 1, frac, false, nullptr, nullptr, df, out_df));
   }
-  SLDG_TRY(compute_fields(c, buf, df));
-  if (Wslot) {
-    KTimer t(c, SLDG_K_OTHER);
-    SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, Wslot, c->stream, Wcounter));
+  return SLDG_OK;
+}
+
+// ---- splitting compositions -------------------------------------------------------
+// A step is a list of stages: drifts (X1 X2 by frac tau) and kicks (the
+// field of the current rho, then V1 V2 by frac tau).  Order 2 is the Strang
+// step of Sec. 2, D(1/2) K(1) D(1/2).  Order 4 (SLDG_FLAG_ORDER4) is the
+// triple jump S(w1 tau) S(w0 tau) S(w1 tau) of Strang steps with Yoshida's
+// weights w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1.  Merged drifts
+// (SLDG_FLAG_MERGE_DRIFTS) join the drift that ends one Strang sub-step and
+// the drift that starts the next.
+struct Stage {
+  bool kick;
+  bool W;  // the first kick of a step: W of its field is recorded
+  double frac;
+};
+
+int strang_weights(const sldg_ctx* c, double* w) {
+  if (c->cfg.flags & SLDG_FLAG_ORDER4) {
+    w[0] = w[2] = 1.0 / (2.0 - std::cbrt(2.0));
+    w[1] = 1.0 - 2.0 * w[0];
+    return 3;
   }
-  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_x12(c, buf, df, false, &fused));
-  if (!fused) {
-    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
-    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
+  w[0] = 1.0;
+  return 1;
+}
+
+bool merged(const sldg_ctx* c) { return (c->cfg.flags & SLDG_FLAG_MERGE_DRIFTS) != 0; }
+
+// one step without merging: D(w/2) K(w) D(w/2) per weight
+std::vector<Stage> step_stages(const sldg_ctx* c) {
+  double w[3];
+  const int n = strang_weights(c, w);
+  std::vector<Stage> st;
+  for (int i = 0; i < n; ++i) {
+    st.push_back({false, false, 0.5 * w[i]});
+    st.push_back({true, i == 0, w[i]});
+    st.push_back({false, false, 0.5 * w[i]});
   }
+  return st;
+}
+
+// merged drifts: a call of n steps is D(w_0/2), then per step the body
+// K(w_0) D((w_0 + w_1)/2) ... K(w_last) D(tail), tail = (w_last + w_0)/2
+// before another step of the call and w_last/2 after the last one
+std::vector<Stage> merged_body(const sldg_ctx* c, bool last) {
+  double w[3];
+  const int n = strang_weights(c, w);
+  std::vector<Stage> st;
+  for (int i = 0; i < n; ++i) {
+    st.push_back({true, i == 0, w[i]});
+    const double next = i + 1 < n ? w[i + 1] : (last ? 0.0 : w[0]);
+    st.push_back({false, false, 0.5 * (w[i] + next)});
+  }
+  return st;
+}
+
+// Run stages in place on buf.  FP64 storage with double-float sweeps: buf
+// holds IEEE doubles where in_ieee / out_ieee say so (the call's first
+// input, its last output) and double-float (hi, lo) pairs in the same
+// 8-byte elements between stages, so the conversions to and from the FP32
+// pipe's format happen once per call.  W of each recorded kick goes to
+// Wbase[*wi] (then ++*wi), or with Wcounter to Wbase[*Wcounter] (a device
+// counter the energy kernel advances; graph capture).
+int run_stages(sldg_ctx* c, void* buf, const std::vector<Stage>& st, bool in_ieee, bool out_ieee,
+               double* Wbase, int* Wcounter, int* wi) {
+  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+  const int n = (int)st.size();
+  for (int q = 0; q < n; ++q) {
+    const bool in_df = df && (q > 0 || !in_ieee);
+    const bool out_df = df && (q + 1 < n || !out_ieee);
+    if (!st[q].kick) {
+      SLDG_TRY(drift(c, buf, st[q].frac, in_df, out_df));
+      continue;
+    }
+    SLDG_TRY(compute_fields(c, buf, in_df));
+    if (st[q].W && Wbase) {
+      KTimer t(c, SLDG_K_OTHER);
+      double* slot = Wcounter ? Wbase : Wbase + *wi;
+      SLDG_CU(launch_energy(c->d_E[0], c->d_E[1], c->d_wx, c->g.Dx, slot, c->stream, Wcounter));
+    }
+    if (st[q].W) ++*wi;
+    SLDG_TRY(run_sweep(c, buf, 2, st[q].frac, false, nullptr, nullptr, in_df, df));
+    SLDG_TRY(run_sweep(c, buf, 3, st[q].frac, false, nullptr, nullptr, df, out_df));
+  }
+  return SLDG_OK;
+}
+
+// One step (order 2 or 4, drifts not merged) in place on buf, IEEE in and
+// out; W of its (first) kick field to Wslot (device) if given.
+int do_step(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter = nullptr) {
+  int wi = 0;
+  return run_stages(c, buf, step_stages(c), true, true, Wslot, Wcounter, &wi);
+}
+
+// The x-matrices of every drift fraction a step of this context uses.
+int prepare_xmats(sldg_ctx* c) {
+  std::vector<Stage> all = step_stages(c);
+  if (merged(c)) {
+    for (bool last : {false, true}) {
+      std::vector<Stage> b = merged_body(c, last);
+      all.insert(all.end(), b.begin(), b.end());
+    }
+  }
+  MatSet* m;
+  for (const Stage& q : all)
+    if (!q.kick)
+      for (int d = 0; d < 2; ++d) SLDG_TRY(ensure_xmats(c, d, q.frac, false, &m));
   return SLDG_OK;
 }
 
@@ -472,12 +594,7 @@ int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_
     }
     return SLDG_OK;
   };
-  bool fused = false;
-  SLDG_TRY(run_x12(c, buf, false, df, &fused));
-  if (!fused) {
-    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, false, df));
-    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, df));
-  }
+  SLDG_TRY(drift(c, buf, 0.5, false, df));
   SLDG_TRY(compute_fields(c, buf, df));
   if (E_out) {
     SLDG_CU(cudaMemcpyAsync(E_out, c->d_E[0], c->g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -490,19 +607,23 @@ int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_
   if (!full) return take(g3_out);
   SLDG_TRY(take(g3_out));
   SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
-  SLDG_TRY(run_x12(c, buf, df, false, &fused));
-  if (!fused) {
-    SLDG_TRY(run_sweep(c, buf, 0, 0.5, false, nullptr, nullptr, df, df));
-    SLDG_TRY(run_sweep(c, buf, 1, 0.5, false, nullptr, nullptr, df, false));
-  }
-  return SLDG_OK;
+  return drift(c, buf, 0.5, df, false);
 }
 
-// nsteps Strang steps of f as replays of one recorded step (a CUDA graph),
-// W of each step to Wbase[counter++] (nullable; the device counter restarts
-// at 0 when reset_counter).  *replayed stays false when graphs do not apply
-// (fewer than two steps, per-kernel timing on, or an earlier capture failed)
-// and the caller runs the steps eagerly.
+// The repeated unit of sldg_step: a whole step (IEEE in and out), or with
+// merged drifts the body of a step that another step follows (double-float
+// pairs in and out on FP64 storage).
+int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter) {
+  int wi = 0;
+  if (merged(c)) return run_stages(c, buf, merged_body(c, false), false, false, Wslot, Wcounter, &wi);
+  return run_stages(c, buf, step_stages(c), true, true, Wslot, Wcounter, &wi);
+}
+
+// nsteps units of f as replays of one recorded unit (a CUDA graph), W of
+// each to Wbase[counter++] (nullable; the device counter restarts at 0 when
+// reset_counter).  *replayed stays false when graphs do not apply (fewer
+// than two units, per-kernel timing on, or an earlier capture failed) and
+// the caller runs the units eagerly.
 int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed) {
   const int hv = Wbase ? 1 : 0;
   *replayed = false;
@@ -510,8 +631,7 @@ int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, boo
     // one recorded step replayed nsteps times: the launch overhead of the
     // small kernels goes away on small grids
     // everything the step allocates lazily exists before the capture
-    SLDG_TRY(ensure_xmats(c, 0, 0.5));
-    SLDG_TRY(ensure_xmats(c, 1, 0.5));
+    SLDG_TRY(prepare_xmats(c));
     for (int d = 0; d < 2; ++d) SLDG_TRY(alloc_matset(c, &c->vm[d], c->g.Dx, false, false));
     if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
     if (c->step_graph[hv] && (c->step_graph_buf[hv] != c->f || c->step_graph_W[hv] != Wbase)) {
@@ -522,7 +642,7 @@ int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, boo
       const long long l0 = c->launches;
       cudaGraph_t graph = nullptr;
       bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      const int rc = ok ? do_step(c, c->f, Wbase, hv ? c->d_counter : nullptr) : SLDG_ERR_CUDA;
+      const int rc = ok ? run_unit(c, c->f, Wbase, hv ? c->d_counter : nullptr) : SLDG_ERR_CUDA;
       if (ok) ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && rc == SLDG_OK;
       if (ok) ok = cudaGraphInstantiate(&c->step_graph[hv], graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
@@ -786,14 +906,31 @@ int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
   if (!c) return SLDG_ERR_BAD_PTR;
   if (nsteps < 0) return SLDG_ERR_ARG;
   if (W_history) SLDG_TRY(ensure_W(c, nsteps));
+  double* Wd = W_history ? c->d_W : nullptr;
+  // merged drifts: D(w_0/2), nsteps - 1 bodies (replayed), the last body
+  const bool mg = merged(c) && nsteps > 0;
+  const int units = mg ? nsteps - 1 : nsteps;
+  if (mg) {
+    double w[3];
+    strang_weights(c, w);
+    int wi = 0;
+    SLDG_TRY(run_stages(c, c->f, {{false, false, 0.5 * w[0]}}, true, false, nullptr, nullptr, &wi));
+  }
   bool replayed = false;
-  SLDG_TRY(replay_steps(c, nsteps, W_history ? c->d_W : nullptr, true, &replayed));
+  SLDG_TRY(replay_steps(c, units, Wd, true, &replayed));
   if (!replayed)
-    for (int m = 0; m < nsteps; ++m) {
-      SLDG_TRY(do_step(c, c->f, W_history ? c->d_W + m : nullptr));
+    for (int m = 0; m < units; ++m) {
+      SLDG_TRY(run_unit(c, c->f, Wd ? Wd + m : nullptr, nullptr));
       c->t += c->g.dt;
       c->step += 1;
     }
+  if (mg) {
+    int wi = 0;
+    SLDG_TRY(run_stages(c, c->f, merged_body(c, true), false, true, Wd ? Wd + units : nullptr,
+                        nullptr, &wi));
+    c->t += c->g.dt;
+    c->step += 1;
+  }
   if (W_history && nsteps > 0) {
     SLDG_CU(cudaMemcpyAsync(W_history, c->d_W, nsteps * sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream));
@@ -948,6 +1085,7 @@ int sldg_sweep_adjoint(sldg_ctx* c, int dim, double frac, void* lam, const void*
 
 int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   if (!c) return SLDG_ERR_BAD_PTR;
+  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS)) return SLDG_ERR_UNSUPPORTED;
   if (nsteps < 1 || ckpt_every < 1) return SLDG_ERR_ARG;
   const size_t fb = c->g.N * c->esize;
   const size_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
@@ -1136,6 +1274,7 @@ extern "C" {
 
 int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
   if (!c || !grad) return SLDG_ERR_BAD_PTR;
+  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS)) return SLDG_ERR_UNSUPPORTED;
   if (!c->recorded) return SLDG_ERR_STATE;
   const Grid& g = c->g;
   const int n = c->rec_nsteps, ck = c->rec_ckpt;

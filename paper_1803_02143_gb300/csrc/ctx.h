@@ -95,7 +95,11 @@ struct sldg_ctx {
   float2* d_wv2 = nullptr; // the same weights as (hi, lo) float pairs
   double* d_wx = nullptr;  // x-plane weights w_x1 * w_x2, Dx doubles
 
-  sldg::MatSet xm[2];  // x1: key v1 node, x2: key v2 node
+  // x1: key v1 node, x2: key v2 node; a few shift fractions at a time (the
+  // drifts of the order-4 and merged splittings use up to three)
+  static constexpr int kXSlots = 6;
+  sldg::MatSet xm[2][kXSlots];
+  int xm_next[2] = {0, 0};  // slot replaced next when all are taken
   sldg::MatSet vm[2];  // v1, v2: key x-node
 
   // fields
@@ -154,8 +158,9 @@ struct sldg_ctx {
   double* h_W = nullptr;
   int h_W_cap = 0;
 
-  // sldg_step as a replayed CUDA graph of one Strang step (two variants:
-  // without / with the W history, whose slot comes from a device counter)
+  // sldg_step as a replayed CUDA graph of one step (two variants: without /
+  // with the W history, whose slot comes from a device counter); with merged
+  // drifts the graph holds the part of a step between two merged drifts
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
   const void* step_graph_buf[2] = {nullptr, nullptr};  // f and W history they were made for
   const void* step_graph_W[2] = {nullptr, nullptr};
