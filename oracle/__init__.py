@@ -20,7 +20,10 @@ form, the convergence order l+1 and the linear Landau damping rate from the
 dispersion relation; the adjoint against dot-product identities and central
 finite differences; the splitting compositions (order 4, merged drifts)
 against the tabulated triple-jump weights, the convergence orders of an
-exactly split pendulum, free streaming and linear Landau damping.
+exactly split pendulum, free streaming and linear Landau damping; the
+cubic-spline advection against scipy's periodic CubicSpline, a dense
+solve of its cyclic system, permutations, conservation, fourth-order
+convergence and free streaming.
 """
 from __future__ import annotations
 
@@ -65,6 +68,7 @@ class _CGrid(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("vbc", ctypes.c_int),
         ("kmax", ctypes.c_int),
+        ("spline", ctypes.c_int),
     ]
 
 
@@ -103,6 +107,9 @@ def _lib_handle():
             "orc_init": (ctypes.c_int, [G, ctypes.c_int, _DP, _DP]),
             "orc_step": (ctypes.c_int, [G, _DP, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP]),
             "orc_fields_of": (ctypes.c_int, [G, _DP, _DP, _DP, _DP]),
+            "orc_spline_coeffs": (ctypes.c_int, [ctypes.c_long, _DP, _DP]),
+            "orc_spline_line": (ctypes.c_int, [ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                               _DP, _DP]),
             "orc_split_stages": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP,
                                                 _DP, ctypes.c_int]),
             "orc_step_split": (ctypes.c_int, [G, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -138,6 +145,7 @@ class Grid:
     dt: float
     vbc: int = 0
     kmax: int = -1
+    spline: int = 0  # 1: cubic-spline sweeps (degree 0, periodic v)
     _c: _CGrid = field(default=None, repr=False, compare=False)
 
     def c(self):
@@ -150,6 +158,7 @@ class Grid:
         g.dt = float(self.dt)
         g.vbc = int(self.vbc)
         g.kmax = int(self.kmax)
+        g.spline = int(self.spline)
         self._c = g
         return ctypes.byref(g)
 
@@ -339,6 +348,24 @@ def step(g: Grid, f, nsteps: int = 1, kick: bool = True):
     if rc != 0:
         raise MemoryError("orc_step failed")
     return f, W[:nsteps], E1, E2
+
+
+def spline_coeffs(u):
+    """B-spline coefficients of the periodic cubic interpolant of u."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.zeros_like(u)
+    if _lib_handle().orc_spline_coeffs(u.size, _p(u), _p(w)) != 0:
+        raise ValueError("orc_spline_coeffs failed")
+    return w
+
+
+def spline_line(h: float, a: float, u):
+    """The periodic cubic-spline advection of Sec. 3: out_i = u~(x_i - a)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    if _lib_handle().orc_spline_line(u.size, float(h), float(a), _p(u), _p(out)) != 0:
+        raise ValueError("orc_spline_line failed")
+    return out
 
 
 def split_stages(order: int, nsteps: int, merge: bool = False):

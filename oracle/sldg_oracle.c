@@ -46,6 +46,8 @@ typedef struct {
   double dt;      /* time step tau */
   int vbc;        /* 0: zero inflow in v, 1: periodic in v */
   int kmax;       /* Poisson modes per direction, < 0: min(nc-1, (D-1)/2) */
+  int spline;     /* 1: sweeps by cubic-spline interpolation (degree 0 grid,
+                     periodic in every direction), see orc_spline_line */
 } orc_grid;
 
 /* ------------------------------------------------------------------------ */
@@ -293,6 +295,84 @@ long orc_numel(const orc_grid* g) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The spline method of Sec. 3 for the same 1D advection, on n equidistant   */
+/* points x_i (spacing h, periodic): the interpolant                          */
+/*   u~(x) = sum_k w_k S(x - x_k),                                            */
+/*   6 S(x) = 4 - 6 (x/h)^2 + 3 |x/h|^3 (|x| <= h), (2 - |x/h|)^3 (h <= |x|    */
+/*   <= 2h), 0 beyond,                                                        */
+/* has coefficients from the cyclic tridiagonal system                        */
+/*   (w_{i-1} + 4 w_i + w_{i+1}) / 6 = u_i   (indices mod n),                 */
+/* and the new values are u~(x_i - a).  The cyclic system is solved with the  */
+/* Thomas algorithm on the tridiagonal part and a rank-one (Sherman-          */
+/* Morrison) correction for the two corner entries.                           */
+/* ------------------------------------------------------------------------ */
+static void thomas(long n, const double* sub, const double* dia, const double* sup,
+                   const double* rhs, double* x, double* cp) {
+  /* forward elimination (cp: modified super-diagonal), back substitution */
+  double den = dia[0];
+  cp[0] = sup[0] / den;
+  x[0] = rhs[0] / den;
+  for (long i = 1; i < n; ++i) {
+    den = dia[i] - sub[i] * cp[i - 1];
+    cp[i] = sup[i] / den;
+    x[i] = (rhs[i] - sub[i] * x[i - 1]) / den;
+  }
+  for (long i = n - 2; i >= 0; --i) x[i] -= cp[i] * x[i + 1];
+}
+
+int orc_spline_coeffs(long n, const double* u, double* w) {
+  if (n < 3) return -1;
+  double* sub = (double*)malloc((size_t)n * 6 * sizeof(double));
+  if (!sub) return -3;
+  double *dia = sub + n, *sup = dia + n, *y = sup + n, *z = y + n, *cp = z + n;
+  /* A = B + p q^T with p = (g, 0, .., 0, 1/6), q = (1, 0, .., 0, (1/6)/g),
+     g = -4/6: B is tridiagonal with its two corner diagonal entries changed */
+  const double off = 1.0 / 6.0, d = 4.0 / 6.0, g = -d;
+  for (long i = 0; i < n; ++i) {
+    sub[i] = off;
+    dia[i] = d;
+    sup[i] = off;
+  }
+  dia[0] = d - g;
+  dia[n - 1] = d - off * off / g;
+  thomas(n, sub, dia, sup, u, y, cp);
+  for (long i = 0; i < n; ++i) w[i] = 0.0;
+  w[0] = g;
+  w[n - 1] = off;
+  thomas(n, sub, dia, sup, w, z, cp);
+  const double qy = y[0] + off / g * y[n - 1], qz = z[0] + off / g * z[n - 1];
+  const double fac = qy / (1.0 + qz);
+  for (long i = 0; i < n; ++i) w[i] = y[i] - fac * z[i];
+  free(sub);
+  return 0;
+}
+
+/* out_i = u~(x_i - a): with a/h = s + theta (s integer, 0 <= theta < 1) the
+   point x_i - a lies theta h before x_{i-s}, and the four B-splines there
+   give  6 out_i = theta^3 w_{i-s-2} + (4 - 6 (1-theta)^2 + 3 (1-theta)^3)
+   w_{i-s-1} + (4 - 6 theta^2 + 3 theta^3) w_{i-s} + (1-theta)^3 w_{i-s+1}. */
+int orc_spline_line(long n, double h, double a, const double* u, double* out) {
+  double* w = (double*)malloc((size_t)n * sizeof(double));
+  if (!w) return -3;
+  int rc = orc_spline_coeffs(n, u, w);
+  if (rc) {
+    free(w);
+    return rc;
+  }
+  long s;
+  double th;
+  split_shift(a, h, &s, &th);
+  const double om = 1.0 - th;
+  const double b0 = th * th * th, b1 = 4.0 - 6.0 * om * om + 3.0 * om * om * om;
+  const double b2 = 4.0 - 6.0 * th * th + 3.0 * th * th * th, b3 = om * om * om;
+  for (long i = 0; i < n; ++i)
+    out[i] = (b0 * w[wrap(i - s - 2, n)] + b1 * w[wrap(i - s - 1, n)] + b2 * w[wrap(i - s, n)] +
+              b3 * w[wrap(i - s + 1, n)]) / 6.0;
+  free(w);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A sweep: the 1D advection applied to every line along direction d.        */
 /*   d = 0 (x1): shift a = v1(node) * dt * frac, periodic  (e^{tau A_1})     */
 /*   d = 1 (x2): shift a = v2(node) * dt * frac, periodic  (e^{tau A_2})     */
@@ -320,10 +400,12 @@ static int sweep_impl(const orc_grid* g, int d, const double* Ed, double frac,
     if (e != d) o[k++] = e;
   int periodic = (d < 2) ? 1 : (g->vbc == 1);
   double h = cellw(g, d);
+  if (g->spline && (mode != 0 || !periodic || g->deg != 0)) return -1;
   long Dx = D[0] * D[1];
   /* Ebar contributions are kept per line so the per-x-node sum can run in a
      fixed order afterwards, independent of the thread count. */
   double* lined = (Ebar && mode == 1) ? (double*)calloc((size_t)nlines, sizeof(double)) : NULL;
+  int failed = 0;
 
 #pragma omp parallel
   {
@@ -344,7 +426,12 @@ static int sweep_impl(const orc_grid* g, int d, const double* Ed, double frac,
       else if (d == 1) a = node_coord(g, 3, idx[3], xi) * g->dt * frac;
       else a = Ed[idx[1] * D[0] + idx[0]] * g->dt * frac;
       for (long i = 0; i < len; ++i) a_in[i] = fin[base + i * S[d]];
-      if (mode == 0) {
+      if (mode == 0 && g->spline) {
+        if (orc_spline_line(len, h, a, a_in, a_out) != 0) {
+#pragma omp atomic write
+          failed = 1;
+        }
+      } else if (mode == 0) {
         orc_advect_line(g->deg, g->nc[d], h, a, periodic, a_in, a_out);
       } else {
         orc_advect_line_adj(g->deg, g->nc[d], h, a, periodic, a_in, a_out);
@@ -365,7 +452,7 @@ static int sweep_impl(const orc_grid* g, int d, const double* Ed, double frac,
     for (long L = 0; L < nlines; ++L) Ebar[L % Dx] += lined[L];
     free(lined);
   }
-  return 0;
+  return failed ? -1 : 0;
 }
 
 int orc_sweep(const orc_grid* g, int d, const double* Ed, double frac, const double* fin,
