@@ -270,21 +270,29 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
     hbm = {"achieved": algo_bytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": algo_bytes / avg_s / 1e9 / pk["hbm_gbs"], "peak_source": peak_src}
     native = cfg.flags & 1
-    if cfg.precision == "fp64" and not native and kind == "x12":
-        # two double-float sweeps per byte: bound by FP32-pipe issue.  Each
-        # lane of a double-float multiply-accumulate is 12 FP32 operations
-        # (product, its FMA error, TwoSum, two low-word adds, two cross FMAs)
-        clk = pk.get("sm_max_mhz", 2070.0)
-        ops = 2 * cfg.numel * (2 * n) * DF_OPS_PER_MAC
+    spline = cfg.flags & 16
+    clk = pk.get("sm_max_mhz", 2070.0)
+    per_kernel = {k: v[0] / steps_timed for k, v in timing.items() if v[1]}
+    if cfg.precision == "fp64" and not native and not spline:
+        # double-float sweeps: each lane of a double-float multiply-accumulate
+        # is 12 FP32 operations (product, its FMA error, TwoSum, two low-word
+        # adds, two cross FMAs); the fused pass does two sweeps per byte.  The
+        # bound is the roofline with the longer floor for this launch.
+        sweeps_per_launch = 2 if kind == "x12" else 1
+        ops = sweeps_per_launch * cfg.numel * (2 * n) * DF_OPS_PER_MAC
         peak_t = SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12
-        return {"bound": "alu", "achieved": ops / avg_s / 1e12, "peak": peak_t,
-                "unit": "T FP32 ops/s", "frac": ops / avg_s / 1e12 / peak_t, "traffic": traffic,
-                "kernel": f"sweep_{kind}",
-                "peak_source": "FP32 lanes x max SM clock (152 SMs x 128 lanes)",
-                "hbm": hbm, "avg_launch_ms": ms / cnt,
-                "per_kernel_ms_per_step": {k: v[0] / steps_timed for k, v in timing.items() if v[1]}}
+        if ops / (peak_t * 1e12) > algo_bytes / (pk["hbm_gbs"] * 1e9):
+            return {"bound": "alu", "achieved": ops / avg_s / 1e12, "peak": peak_t,
+                    "unit": "T FP32 ops/s", "frac": ops / avg_s / 1e12 / peak_t,
+                    "traffic": traffic, "kernel": f"sweep_{kind}",
+                    "peak_source": "FP32 lanes x max SM clock (152 SMs x 128 lanes)",
+                    "hbm": hbm, "avg_launch_ms": ms / cnt, "per_kernel_ms_per_step": per_kernel}
+    if cfg.precision == "fp64" and spline:
+        # cubic-spline sweeps in FP64 arithmetic: per point one FMA in each of
+        # the two recurrences of the cyclic solve and four in the evaluation
+        algo_flops = 2 * 6 * cfg.numel
+        native = True
     if cfg.precision == "fp64" and native:
-        clk = pk.get("sm_max_mhz", 2070.0)
         peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": algo_flops / avg_s / 1e12, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": algo_flops / avg_s / 1e12 / peak_tf,
@@ -296,7 +304,7 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
                 "frac": hbm["frac"], "traffic": traffic, "kernel": f"sweep_{kind}",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
     roof["avg_launch_ms"] = ms / cnt
-    roof["per_kernel_ms_per_step"] = {k: v[0] / steps_timed for k, v in timing.items() if v[1]}
+    roof["per_kernel_ms_per_step"] = per_kernel
     return roof
 
 

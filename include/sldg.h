@@ -81,8 +81,19 @@ extern "C" {
                                    drifts (the SLDG projection does not compose
                                    exactly), so steps of different calls differ
                                    from one call of all the steps */
-/* sldg_record and sldg_backward differentiate the Strang step: with ORDER4
- * or MERGE_DRIFTS they return SLDG_ERR_UNSUPPORTED. */
+#define SLDG_FLAG_SPLINE 16     /* the comparison method of Sec. 3: every sweep is
+                                   the cubic-spline advection (periodic cubic
+                                   B-spline interpolant of the point values,
+                                   evaluated at the shifted points) instead of
+                                   the SLDG projection.  Needs degree 0 (one
+                                   point per cell: a uniform grid of cell
+                                   centres), SLDG_VBC_PERIODIC and ncell >= 3;
+                                   rho, Poisson and the diagnostics are those
+                                   of the degree-0 grid (midpoint sums).  FP64
+                                   storage sweeps in FP64 arithmetic. */
+/* sldg_record and sldg_backward differentiate the Strang step of the SLDG
+ * sweeps: with ORDER4, MERGE_DRIFTS or SPLINE they return
+ * SLDG_ERR_UNSUPPORTED, and so does sldg_sweep_adjoint with SPLINE. */
 
 #define SLDG_VBC_ZERO_INFLOW 0 /* v-sweeps drop source cells outside the box */
 #define SLDG_VBC_PERIODIC 1    /* v-sweeps wrap (test mode: exact mass) */
@@ -144,7 +155,8 @@ int sldg_abi_version(void);
  * nodes, the x-sweep matrices (one pair per v-node, Sec. 3: "precomputed") and
  * the spectral tables.  f_dev is not read or written here.
  * Errors: BAD_CONFIG (degree outside 0..3, ncell < 2, hi <= lo, dt <= 0,
- * unknown precision/vbc, unknown flag bits, a line too long for on-chip staging),
+ * unknown precision/vbc, unknown flag bits, SLDG_FLAG_SPLINE without degree
+ * 0, periodic v and ncell >= 3, a line too long for on-chip staging),
  * BAD_PTR (cfg or out NULL, f_dev NULL or misaligned), OOM, CUDA. */
 int sldg_init(const sldg_config* cfg, void* f_dev, void* stream, sldg_ctx** out);
 
@@ -241,8 +253,8 @@ int sldg_sweep_adjoint(sldg_ctx* ctx, int dim, double frac, void* lam, const voi
  * checkpoint of f every ckpt_every steps in a library-owned device pool
  * (ceil(nsteps / ckpt_every) copies of f), and record W of each step
  * (W_history, host, nullable).  Prepares sldg_backward.
- * Errors: ARG, OOM (the pool does not fit), UNSUPPORTED (SLDG_FLAG_ORDER4 or
- * SLDG_FLAG_MERGE_DRIFTS), CUDA. */
+ * Errors: ARG, OOM (the pool does not fit), UNSUPPORTED (SLDG_FLAG_ORDER4,
+ * SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE), CUDA. */
 int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
 
 /* Reverse pass of the last sldg_record: gradient of
@@ -263,7 +275,8 @@ int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
  * step.  The gradient is the same whatever the number of slots (the same
  * arithmetic, only repeated).
  * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits),
- * UNSUPPORTED (SLDG_FLAG_ORDER4 or SLDG_FLAG_MERGE_DRIFTS), CUDA. */
+ * UNSUPPORTED (SLDG_FLAG_ORDER4, SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE),
+ * CUDA. */
 int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
 
 /* Upper bound on the recomputation slots of sldg_backward (0 = as many as a

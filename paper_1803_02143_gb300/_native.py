@@ -29,6 +29,7 @@ SLDG_FLAG_NATIVE_FP64 = 1
 SLDG_FLAG_NO_XFUSION = 2
 SLDG_FLAG_ORDER4 = 4
 SLDG_FLAG_MERGE_DRIFTS = 8
+SLDG_FLAG_SPLINE = 16
 SLDG_VBC_ZERO_INFLOW = 0
 SLDG_VBC_PERIODIC = 1
 SLDG_INIT_LANDAU = 0

@@ -70,6 +70,13 @@ WORKLOADS = {
         f"two_stream_paper_dg4_{nc}",
         Config(degree=3, ncell=(nc,) * 4, lo=TSI_PAPER_LO, hi=TSI_PAPER_HI, dt=0.1),
         N.SLDG_INIT_TWO_STREAM_PAPER, (1e-3, 0.2, 2.4), 2500) for nc in (8, 16, 32)},
+    # the cubic-spline comparison method of Sec. 3 (Table 1: 64 and 128 grid
+    # points per direction) on nonlinear Landau damping, dt 0.1, periodic v
+    **{f"spline_landau_{n}": Workload(
+        f"spline_landau_{n}",
+        Config(degree=0, ncell=(n,) * 4, lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1, vbc=1,
+               flags=N.SLDG_FLAG_SPLINE),
+        N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 500) for n in (64, 128)},
     # adjoint of nonlinear Landau damping, 32^4 cells, degree 1, dt 0.1, 100 steps, ckpt 10
     "adjoint_landau_32": Workload("adjoint_landau_32", _landau(1, 32, 0.1, 0.5), N.SLDG_INIT_LANDAU,
                                   (0.5, 0.5, 0.5), 100, ckpt=10),
@@ -80,7 +87,10 @@ WORKLOADS = {
 
 
 def workload(name: str, precision: str | None = None, flags: int = 0) -> Workload:
+    """The named workload, in another storage precision and with more
+    configuration flags (added to the workload's own) if given."""
     w = WORKLOADS[name]
+    flags = flags | w.cfg.flags
     if (precision is None or precision == w.cfg.precision) and flags == w.cfg.flags:
         return w
     c = w.cfg

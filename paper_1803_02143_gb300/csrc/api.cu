@@ -146,8 +146,13 @@ int validate(const sldg_config* cfg) {
   if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
   if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
   if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION | SLDG_FLAG_ORDER4 |
-                     SLDG_FLAG_MERGE_DRIFTS))
+                     SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
     return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & SLDG_FLAG_SPLINE) {
+    if (cfg->degree != 0 || cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
+    for (int d = 0; d < 4; ++d)
+      if (cfg->ncell[d] < 3) return SLDG_ERR_BAD_CONFIG;
+  }
   return SLDG_OK;
 }
 
@@ -238,6 +243,14 @@ int alloc_matset(sldg_ctx* c, MatSet* m, long long count, bool deriv, bool trans
   return SLDG_OK;
 }
 
+bool spline(const sldg_ctx* c) { return (c->cfg.flags & SLDG_FLAG_SPLINE) != 0; }
+
+// FP64 storage swept in double-float arithmetic, whose states between the
+// stages of a step are (hi, lo) pairs
+bool df_states(const sldg_ctx* c) {
+  return c->prec == SLDG_FP64 && !(c->cfg.flags & (SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE));
+}
+
 void drop_step_graphs(sldg_ctx* c) {
   for (int i = 0; i < 2; ++i) {
     if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
@@ -273,9 +286,13 @@ int ensure_xmats(sldg_ctx* c, int d, double frac, bool trans, MatSet** out) {
   const int vd = d + 2;
   SLDG_TRY(alloc_matset(c, &m, c->g.D[vd], false, trans));
   KTimer t(c, SLDG_K_VMAT);
-  SLDG_CU(launch_build_mats(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], c->basis,
-                            m.ab, nullptr, m.ab2, m.s, c->stream, trans ? m.abt : nullptr,
-                            trans ? m.abt2 : nullptr, trans ? m.st : nullptr));
+  if (spline(c))
+    SLDG_CU(launch_spline_shifts(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], m.ab,
+                                 m.s, c->stream));
+  else
+    SLDG_CU(launch_build_mats(c->prec, m.count, c->d_z[vd], c->g.dt, frac, c->g.h[d], c->basis,
+                              m.ab, nullptr, m.ab2, m.s, c->stream, trans ? m.abt : nullptr,
+                              trans ? m.abt2 : nullptr, trans ? m.st : nullptr));
   m.frac = frac;
   m.valid = true;
   m.with_t = trans;
@@ -289,6 +306,15 @@ int ensure_vmats(sldg_ctx* c, int d, double frac, bool deriv, bool trans = false
   if (m.valid && m.frac == frac && (!deriv || m.with_deriv) && (!trans || m.with_t)) return SLDG_OK;
   SLDG_TRY(alloc_matset(c, &m, c->g.Dx, deriv, trans));
   KTimer t(c, SLDG_K_VMAT);
+  if (spline(c)) {
+    SLDG_CU(launch_spline_shifts(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], m.ab,
+                                 m.s, c->stream));
+    m.frac = frac;
+    m.valid = true;
+    m.with_deriv = false;
+    m.with_t = false;
+    return SLDG_OK;
+  }
   SLDG_CU(launch_build_mats(c->prec, m.count, c->d_E[d], c->g.dt, frac, c->g.h[d + 2], c->basis,
                             m.ab, deriv ? m.dab : nullptr, m.ab2, m.s, c->stream,
                             trans ? m.abt : nullptr, trans ? m.abt2 : nullptr,
@@ -307,6 +333,7 @@ void invalidate_vmats(sldg_ctx* c) { c->vm[0].valid = c->vm[1].valid = false; }
 int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const void* gfwd,
               double* Ebar, bool in_df = false, bool out_df = false) {
   const Grid& g = c->g;
+  if (spline(c) && adjoint) return SLDG_ERR_UNSUPPORTED;
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.f = buf;
@@ -393,7 +420,8 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
   {
     KTimer t(c, kind);
     cudaError_t e;
-    if (c->prec == SLDG_FP32) e = launch_sweep_f32(a, c->stream);
+    if (spline(c)) e = launch_spline_sweep(a, c->stream);
+    else if (c->prec == SLDG_FP32) e = launch_sweep_f32(a, c->stream);
     else if (a.adjoint || a.native_fp64) e = launch_sweep_f64(a, c->stream);
     else e = launch_sweep_df(a, c->stream);
     if (e != cudaSuccess) {
@@ -433,7 +461,8 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // layout does not suit it and the two sweeps must run separately.
 int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done) {
   *done = false;
-  if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64)) return SLDG_OK;
+  if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE))
+    return SLDG_OK;
   MatSet *m0, *m1;
   SLDG_TRY(ensure_xmats(c, 0, frac, false, &m0));
   SLDG_TRY(ensure_xmats(c, 1, frac, false, &m1));
@@ -530,7 +559,7 @@ std::vector<Stage> merged_body(const sldg_ctx* c, bool last) {
 // counter the energy kernel advances; graph capture).
 int run_stages(sldg_ctx* c, void* buf, const std::vector<Stage>& st, bool in_ieee, bool out_ieee,
                double* Wbase, int* Wcounter, int* wi) {
-  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+  const bool df = df_states(c);
   const int n = (int)st.size();
   for (int q = 0; q < n; ++q) {
     const bool in_df = df && (q > 0 || !in_ieee);
@@ -583,7 +612,7 @@ int prepare_xmats(sldg_ctx* c) {
 // recomputed trajectory is the recorded one bit for bit.  g3_out may be buf
 // itself when !full (converted in place).  full: finish the step in buf.
 int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_out, bool full) {
-  const bool df = c->prec == SLDG_FP64 && !(c->cfg.flags & SLDG_FLAG_NATIVE_FP64);
+  const bool df = df_states(c);
   const size_t fb = c->g.N * c->esize;
   auto take = [&](void* dst) -> int {  // IEEE copy of the current state
     if (df) {
@@ -1079,13 +1108,15 @@ int sldg_sweep_adjoint(sldg_ctx* c, int dim, double frac, void* lam, const void*
   if (dim < 0 || dim > 3 || !std::isfinite(frac)) return SLDG_ERR_ARG;
   if ((g == nullptr) != (Ebar == nullptr)) return SLDG_ERR_ARG;
   if (g && dim < 2) return SLDG_ERR_ARG;
+  if (spline(c)) return SLDG_ERR_UNSUPPORTED;
   if (g) SLDG_TRY(ensure_adjoint_scratch(c));
   return run_sweep(c, lam, dim, frac, true, g, Ebar);
 }
 
 int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   if (!c) return SLDG_ERR_BAD_PTR;
-  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS)) return SLDG_ERR_UNSUPPORTED;
+  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
+    return SLDG_ERR_UNSUPPORTED;
   if (nsteps < 1 || ckpt_every < 1) return SLDG_ERR_ARG;
   const size_t fb = c->g.N * c->esize;
   const size_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
@@ -1274,7 +1305,8 @@ extern "C" {
 
 int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
   if (!c || !grad) return SLDG_ERR_BAD_PTR;
-  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS)) return SLDG_ERR_UNSUPPORTED;
+  if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
+    return SLDG_ERR_UNSUPPORTED;
   if (!c->recorded) return SLDG_ERR_STATE;
   const Grid& g = c->g;
   const int n = c->rec_nsteps, ck = c->rec_ckpt;

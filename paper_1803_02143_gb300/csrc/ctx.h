@@ -63,6 +63,11 @@ struct SweepArgs {
 // Kernel launchers (sweep_f64.cu / sweep_f32.cu).
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);  // FP64 FMA
 cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st);   // double-float
+// cubic-spline advection (spline.cu): a.ab holds theta per key (context
+// precision), a.s the integer shifts; degree 0, periodic lines of >= 3 points
+cudaError_t launch_spline_sweep(const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_spline_shifts(int prec, long long count, const double* src, double dt,
+                                 double frac, double h, void* theta, int* s, cudaStream_t st);
 // shift-derivative partials of an adjoint v-sweep in double-float (a.f = the
 // adjoint before the sweep, a.g = the forward input, a.dab2, a.s, a.epart)
 cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st);

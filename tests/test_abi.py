@@ -82,7 +82,7 @@ def test_init_rejects_bad_pointers_on_host(lib):
     assert lib.sldg_init(ctypes.byref(c), None, None, ctypes.byref(out)) == N.SLDG_ERR_BAD_PTR
     assert lib.sldg_init(ctypes.byref(c), ctypes.c_void_p(24), None,
                          ctypes.byref(out)) == N.SLDG_ERR_BAD_PTR  # misaligned
-    c.flags = 16  # unknown flag bit
+    c.flags = 32  # unknown flag bit
     assert lib.sldg_init(ctypes.byref(c), ctypes.c_void_p(16), None,
                          ctypes.byref(out)) == N.SLDG_ERR_BAD_CONFIG
 
