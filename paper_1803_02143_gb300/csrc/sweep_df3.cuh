@@ -134,8 +134,25 @@ __device__ __forceinline__ void df3_run(const double* __restrict__ raw, const fl
   df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), uh, ul);
   double* out = fb + c0 + (long long)cb * N * rstride;
   const long long cstep = (long long)N * rstride;
+  int c = cb;
+  if constexpr (N <= 3) {
+    // two cells per iteration, the two register sets trading the a and b
+    // roles (no window copies; 4% faster v-sweeps at 192-node v-lines, and
+    // slower at four nodes per cell, where the registers run out)
 #pragma unroll 1
-  for (int c = cb; c < ce; ++c, out += cstep) {
+    for (; c + 1 < ce; c += 2, out += 2 * cstep) {
+      k0 = next(k0);
+      k1 = next(k1);
+      df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), wh, wl);
+      df3_cell<N, OUT_DF>(M, uh, ul, wh, wl, out, rstride);
+      k0 = next(k0);
+      k1 = next(k1);
+      df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), uh, ul);
+      df3_cell<N, OUT_DF>(M, wh, wl, uh, ul, out + cstep, rstride);
+    }
+  }
+#pragma unroll 1
+  for (; c < ce; ++c, out += cstep) {
     k0 = next(k0);
     k1 = next(k1);
     df3_load_cell<N, SAME>(raw, c0, row(k0), row(k1), wh, wl);
