@@ -87,7 +87,8 @@ extern "C" {
                                    evaluated at the shifted points) instead of
                                    the SLDG projection.  Needs degree 0 (one
                                    point per cell: a uniform grid of cell
-                                   centres), SLDG_VBC_PERIODIC and ncell >= 3;
+                                   centres), SLDG_VBC_PERIODIC and 3 <= ncell <= 440
+                                   (880 for FP32: two tiles of a line on chip);
                                    rho, Poisson and the diagnostics are those
                                    of the degree-0 grid (midpoint sums).  FP64
                                    storage sweeps in FP64 arithmetic. */

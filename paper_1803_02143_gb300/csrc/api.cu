@@ -149,9 +149,12 @@ int validate(const sldg_config* cfg) {
                      SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
     return SLDG_ERR_BAD_CONFIG;
   if (cfg->flags & SLDG_FLAG_SPLINE) {
+    // a spline sweep stages two [n][33] tiles of a line direction on chip
+    const long long esize = cfg->precision == SLDG_FP64 ? 8 : 4;
     if (cfg->degree != 0 || cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
     for (int d = 0; d < 4; ++d)
-      if (cfg->ncell[d] < 3) return SLDG_ERR_BAD_CONFIG;
+      if (cfg->ncell[d] < 3 || 2LL * cfg->ncell[d] * 33 * esize > 227 * 1024)
+        return SLDG_ERR_BAD_CONFIG;
   }
   return SLDG_OK;
 }

@@ -63,7 +63,11 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(degree=4), dict(degree=-1), dict(ncell=(1, 4, 4, 4)),
                                  dict(dt=0.0), dict(dt=float("nan")),
-                                 dict(hi=(0.0, 12.56, 6, 6))])
+                                 dict(hi=(0.0, 12.56, 6, 6)),
+                                 # the spline method: degree 0, periodic v, 3 to 440 points
+                                 dict(degree=1, vbc=1, flags=16), dict(degree=0, vbc=0, flags=16),
+                                 dict(degree=0, vbc=1, flags=16, ncell=(4, 2, 4, 4)),
+                                 dict(degree=0, vbc=1, flags=16, ncell=(441, 4, 4, 4))])
 def test_init_rejects_invalid_config_on_host(lib, bad):
     # validation happens before any CUDA call
     from paper_1803_02143_gb300 import _native as N
