@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -141,29 +142,40 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def csrc_sha1():
-    """SHA-1 of the kernel sources: every file of csrc/ except the host-side
-    ABI implementation (api.cu), which launches the kernels but is not one."""
-    h = hashlib.sha1()
+def unit_sha1(unit):
+    """SHA-1 of one kernel translation unit of csrc/ and every csrc/ header it
+    includes (recursively): the sources of the kernels it instantiates."""
     d = os.path.join(ROOT, "paper_1803_02143_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")) and f != "api.cu":
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
+    seen = []
+
+    def visit(name):
+        path = os.path.join(d, name)
+        if name in seen or not os.path.exists(path):
+            return
+        seen.append(name)
+        with open(path) as fh:
+            for inc in re.findall(r'#include "([^"]+)"', fh.read()):
+                visit(inc)
+
+    visit(unit)
+    h = hashlib.sha1()
+    for name in sorted(seen):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
     return h.hexdigest()
 
 
 def committed_traffic(key):
     """DRAM bytes per launch of a kernel from a committed ncu capture, or None
-    when the kernel sources changed since that capture."""
+    when the sources of its translation unit changed since that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
     e = t.get(key)
-    if not e or e.get("csrc_sha1") != csrc_sha1():
+    if not e or "unit" not in e or e.get("csrc_sha1") != unit_sha1(e["unit"]):
         return None
     return e.get("bytes_per_launch")
 
