@@ -72,17 +72,17 @@ __global__ void __launch_bounds__(kSplThreads)
   }
   T* base = CONTIG ? f + b0 * n : f + b0 * n * inner + j0;
 
-  // stage: every read coalesced (lines, or rows of the column tile)
+  // stage: every read coalesced (a warp along a line, or along a row of the
+  // column tile); the padded pitch keeps the transposed writes conflict-free
+  const int warp = tid / kSplLines, lane = tid % kSplLines;
+  constexpr int kWarps = kSplThreads / kSplLines;
   if (CONTIG) {
-    for (int idx = tid; idx < nl * n; idx += kSplThreads) {
-      const int l = idx / n, i = idx - l * n;
-      U[i * kSplPitch + l] = base[idx];
+    for (int l = warp; l < nl; l += kWarps) {
+      const T* src = base + (long long)l * n;
+      for (int i = lane; i < n; i += kSplLines) U[i * kSplPitch + l] = src[i];
     }
-  } else {
-    for (int idx = tid; idx < n * kSplLines; idx += kSplThreads) {
-      const int i = idx / kSplLines, l = idx - i * kSplLines;
-      if (l < nl) U[i * kSplPitch + l] = base[(long long)i * inner + l];
-    }
+  } else if (lane < nl) {
+    for (int i = warp; i < n; i += kWarps) U[i * kSplPitch + lane] = base[(long long)i * inner + lane];
   }
   __syncthreads();
 
@@ -152,15 +152,12 @@ __global__ void __launch_bounds__(kSplThreads)
   }
   __syncthreads();
   if (CONTIG) {
-    for (int idx = tid; idx < nl * n; idx += kSplThreads) {
-      const int ll = idx / n, i = idx - ll * n;
-      base[idx] = Y[i * kSplPitch + ll];
+    for (int ll = warp; ll < nl; ll += kWarps) {
+      T* dst = base + (long long)ll * n;
+      for (int i = lane; i < n; i += kSplLines) dst[i] = Y[i * kSplPitch + ll];
     }
-  } else {
-    for (int idx = tid; idx < n * kSplLines; idx += kSplThreads) {
-      const int i = idx / kSplLines, ll = idx - i * kSplLines;
-      if (ll < nl) base[(long long)i * inner + ll] = Y[i * kSplPitch + ll];
-    }
+  } else if (lane < nl) {
+    for (int i = warp; i < n; i += kWarps) base[(long long)i * inner + lane] = Y[i * kSplPitch + lane];
   }
 }
 
