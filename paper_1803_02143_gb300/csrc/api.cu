@@ -462,19 +462,27 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // X1(frac tau) X2(frac tau) as one fused pass over each x-plane (FP32 storage,
 // or FP64 storage in double-float arithmetic); *done stays false when the
 // layout does not suit it and the two sweeps must run separately.
-int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done) {
+// trans: the transposed sweeps X1^T then X2^T (the adjoint of the pair, which
+// commute like X1 and X2), run in forward form on the transposed tables
+// ([B^T; A^T], shift entries -s - 1) like the separate adjoint x-sweeps
+int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done,
+            bool trans = false) {
   *done = false;
   if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE))
     return SLDG_OK;
   MatSet *m0, *m1;
-  SLDG_TRY(ensure_xmats(c, 0, frac, false, &m0));
-  SLDG_TRY(ensure_xmats(c, 1, frac, false, &m1));
-  KTimer t(c, SLDG_K_X12);
+  SLDG_TRY(ensure_xmats(c, 0, frac, trans, &m0));
+  SLDG_TRY(ensure_xmats(c, 1, frac, trans, &m1));
+  const int* s0 = trans ? m0->st : m0->s;
+  const int* s1 = trans ? m1->st : m1->s;
+  KTimer t(c, trans ? SLDG_K_ADJ_X : SLDG_K_X12);
   const cudaError_t e =
       c->prec == SLDG_FP32
-          ? launch_sweep_x12_f32(buf, c->g, m0->ab, m0->s, m1->ab, m1->s, c->stream)
-          : launch_sweep_x12_df(buf, c->g, m0->ab2, m0->s, m1->ab2, m1->s, in_df ? 1 : 0,
-                                out_df ? 1 : 0, c->stream);
+          ? launch_sweep_x12_f32(buf, c->g, trans ? m0->abt : m0->ab, s0,
+                                 trans ? m1->abt : m1->ab, s1, c->stream)
+          : launch_sweep_x12_df(buf, c->g, trans ? m0->abt2 : m0->ab2, s0,
+                                trans ? m1->abt2 : m1->ab2, s1, in_df ? 1 : 0, out_df ? 1 : 0,
+                                c->stream);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -1186,6 +1194,18 @@ namespace {
 // grad <- (step m)^T grad + the dJ/dW_m c_m contributions (Eq. AB-sldg
 // transposed, the v-shift derivatives, the Poisson and charge-density
 // adjoints).
+// Adjoint of a half drift X2(tau/2) X1(tau/2) on the adjoint in place: one
+// fused pass of the transposed sweeps, or X2^T then X1^T
+int adjoint_drift(sldg_ctx* c, void* lam) {
+  bool fused = false;
+  SLDG_TRY(run_x12(c, lam, 0.5, false, false, &fused, true));
+  if (!fused) {
+    SLDG_TRY(run_sweep(c, lam, 1, 0.5, true, nullptr, nullptr));
+    SLDG_TRY(run_sweep(c, lam, 0, 0.5, true, nullptr, nullptr));
+  }
+  return SLDG_OK;
+}
+
 int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double* E, int m,
                       const double* cW, void* grad) {
   const Grid& g = c->g;
@@ -1199,8 +1219,7 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
   }
   SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
   SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
-  SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
+  SLDG_TRY(adjoint_drift(c, grad));
   SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1]));
   SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0]));
   {
@@ -1217,9 +1236,7 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
     KTimer t(c, SLDG_K_RHO);
     SLDG_CU(launch_rho_adj(c->prec, grad, g, c->d_wv, c->d_rhob, c->stream));
   }
-  SLDG_TRY(run_sweep(c, grad, 1, 0.5, true, nullptr, nullptr));
-  SLDG_TRY(run_sweep(c, grad, 0, 0.5, true, nullptr, nullptr));
-  return SLDG_OK;
+  return adjoint_drift(c, grad);
 }
 
 // The same from the step's initial state fm (recomputing g2, g3 and the
