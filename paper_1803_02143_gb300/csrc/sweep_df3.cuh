@@ -97,6 +97,27 @@ __device__ __forceinline__ void df3_accumulate(const float4* __restrict__ M, con
   }
 }
 
+// The same for the R outputs j0 .. j0 + R - 1 of a cell only.
+template <int N, int R>
+__device__ __forceinline__ void df3_accumulate_rows(const float4* __restrict__ M, int j0,
+                                                    const float2* ah, const float2* al,
+                                                    const float2* bh, const float2* bl,
+                                                    float2* sh, float2* sl) {
+#pragma unroll
+  for (int t = 0; t < 2 * N; ++t) {
+    asm volatile("" ::: "memory");
+    const float2 xh = t < N ? ah[t] : bh[t - N];
+    const float2 xl = t < N ? al[t] : bl[t - N];
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) {
+      const int j = j0 + jj;
+      const float4 m = M[t < N ? j * N + t : N * N + j * N + (t - N)];
+      if (t == 0) df2_first(make_float2(m.x, m.y), make_float2(m.z, m.w), xh, xl, sh[jj], sl[jj]);
+      else df2_mac(make_float2(m.x, m.y), make_float2(m.z, m.w), xh, xl, sh[jj], sl[jj]);
+    }
+  }
+}
+
 template <int N, bool OUT_DF>
 __device__ __forceinline__ void df3_cell(const float4* __restrict__ M, const float2* ah,
                                          const float2* al, const float2* bh, const float2* bl,
@@ -499,7 +520,12 @@ __device__ __forceinline__ void x1w_load_cell(const float4* __restrict__ pl, int
   }
 }
 
-template <int N, bool IN_DF, bool OUT_DF>
+// HALF (even N): a lane's unit of work is one half of a cell's outputs
+// instead of a run of whole cells, for lines whose cell count leaves many
+// lanes idle at whole cells (36 cells: 18 of 32 lanes busy, against 72
+// half-cells on 32 lanes in three rounds); each unit reads both source
+// cells, the whole-cell run slides over them.
+template <int N, bool IN_DF, bool OUT_DF, bool HALF>
 __global__ void __launch_bounds__(256, N >= 4 ? 2 : 3)
     k_sweep_x1_warp(double* __restrict__ f, int nc, long long npairs, int pairs_per_warp,
                     const float2* __restrict__ ab2, const int* __restrict__ svec, long long mcount,
@@ -559,7 +585,25 @@ __global__ void __launch_bounds__(256, N >= 4 ? 2 : 3)
       pl[k] = make_float4(h0, h1, l0, l1);
     }
     __syncwarp();
-    if (cb < ce) {
+    if constexpr (HALF) {
+      constexpr int R = N / 2;
+      for (int u = lane; u < 2 * nc; u += 32) {
+        const int c = u >> 1, j0 = (u & 1) * R;
+        int ka = c + sa;
+        if (ka >= nc) ka -= nc;
+        const int kb = ka + 1 == nc ? 0 : ka + 1;
+        float2 ah[N], al[N], bh[N], bl[N];
+        x1w_load_cell<N>(pl, ka, ah, al);
+        x1w_load_cell<N>(pl, kb, bh, bl);
+        float2 sh[R], sl[R];
+        df3_accumulate_rows<N, R>(smat, j0, ah, al, bh, bl, sh, sl);
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) {
+          cur[c * N + j0 + jj] = store_pair<OUT_DF>(sh[jj].x, sl[jj].x);
+          cur[D + c * N + j0 + jj] = store_pair<OUT_DF>(sh[jj].y, sl[jj].y);
+        }
+      }
+    } else if (cb < ce) {
       int ka = cb + sa;
       if (ka >= nc) ka -= nc;
       float2 ah[N], al[N], bh[N], bl[N];
@@ -610,7 +654,11 @@ cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st) {
   const long long blocks = (warps + nwarps - 1) / nwarps;
   if (blocks > 0x7fffffffLL) return cudaErrorNotSupported;
   const size_t smem = nwarps * wbytes;
-  auto kfn = k_sweep_x1_warp<N, IN_DF, OUT_DF>;
+  // half-cell units when they keep clearly more lanes busy than whole cells
+  const int nc = a.nc, cpl = (nc + 31) / 32, hr = (2 * nc + 31) / 32;
+  const bool half = (N % 2 == 0) && 2 * cpl > 1.15 * hr;  // busy-lane fractions nc / 32 cpl vs 2 nc / 32 hr
+  auto kfn = half ? k_sweep_x1_warp<N, IN_DF, OUT_DF, (N % 2 == 0)>
+                  : k_sweep_x1_warp<N, IN_DF, OUT_DF, false>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   kfn<<<(unsigned)blocks, nwarps * 32, smem, st>>>(f, a.nc, npairs, kX1WarpPairs,
