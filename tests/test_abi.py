@@ -98,3 +98,28 @@ def test_null_context_is_rejected(lib):
     assert lib.sldg_sweep(None, 0, 0.5) == N.SLDG_ERR_BAD_PTR
     assert lib.sldg_numel(None) == 0
     lib.sldg_destroy(None)
+
+
+def test_every_workload_passes_host_validation(lib):
+    # the configurations of the shipped workloads are valid; without a GPU
+    # sldg_init stops at its first device allocation, with one it succeeds
+    # (f_dev is not touched by sldg_init)
+    from paper_1803_02143_gb300 import _native as N
+    from paper_1803_02143_gb300 import configs
+
+    for name, w in configs.WORKLOADS.items():
+        out = ctypes.c_void_p()
+        rc = lib.sldg_init(ctypes.byref(w.cfg.c()), ctypes.c_void_p(16), None, ctypes.byref(out))
+        assert rc != N.SLDG_ERR_BAD_CONFIG, name
+        if rc == N.SLDG_OK:
+            lib.sldg_destroy(out)
+
+
+def test_workload_flags_are_kept_when_adding_flags():
+    from paper_1803_02143_gb300 import _native as N
+    from paper_1803_02143_gb300 import configs
+
+    w = configs.workload("spline_landau_64", "fp32", N.SLDG_FLAG_ORDER4)
+    assert w.cfg.flags == N.SLDG_FLAG_SPLINE | N.SLDG_FLAG_ORDER4
+    assert w.cfg.precision == "fp32" and w.cfg.vbc == N.SLDG_VBC_PERIODIC
+    assert configs.workload("nonlinear_landau_64") is configs.WORKLOADS["nonlinear_landau_64"]
