@@ -17,7 +17,8 @@ that does not come from the oracle.
 
 The dispersion roots come from the plasma dispersion function; the CPU tests
 pin that routine against the textbook Landau root and against direct
-quadrature of the dielectric function.
+quadrature of the dielectric function, and run the oracle on the same
+two-stream problem.
 """
 import numpy as np
 import pytest
@@ -108,6 +109,22 @@ def _peaks(W, dt, t0, t1):
             tp.append(t[i] + d * dt)
             lp.append(b - 0.25 * (a - c) * d)
     return np.array(tp), np.array(lp)
+
+
+def test_oracle_paper_two_stream_linear_growth(orc):
+    # the oracle alone on the same problem (about 45 s on 16 cores): the
+    # growth of the seeded (k, k) mode is the method's, not the GPU's
+    import math
+
+    g = orc.Grid(deg=3, nc=(8, 8, 8, 8), lo=(0.0, 0.0, -6.0, -6.0),
+                 hi=(10 * math.pi, 10 * math.pi, 6.0, 6.0), dt=0.1)
+    f0 = orc.init(g, orc.TWO_STREAM_PAPER, [1e-3, 0.2, 2.4])
+    _, W, _, _ = orc.step(g, f0, 505)
+    om, ga = root(0.2 * np.sqrt(2), tsi_kk_beams(2.4), [0.6, 0.07])
+    tp, lp = _peaks(W, g.dt, 25.0, 50.0)
+    assert len(tp) >= 4
+    assert abs(np.polyfit(tp, lp, 1)[0] / 2 - ga) < 0.03 * ga
+    assert abs(np.pi / np.mean(np.diff(tp)) - om) < 0.02 * om
 
 
 @pytest.mark.gpu
