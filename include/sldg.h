@@ -13,6 +13,9 @@
  *   f^{m+1} = e^{tau/2 A} e^{tau B} e^{tau/2 A} f^m
  * is a sequence of 1D translations projected back onto the cells
  * (Eq. (AB-sldg): out_i = A(theta) in_{i*} + B(theta) in_{i*+1}).
+ * Configuration flags select the order-4 composition of Strang steps,
+ * merged drifts, or the cubic-spline interpolation of Sec. 3 (the method
+ * the paper compares with) in place of the projection.
  *
  * Conventions of every entry point:
  *   - directions d = 0, 1, 2, 3 are x1, x2, v1, v2;
@@ -49,7 +52,7 @@ extern "C" {
 #define SLDG_ERR_OOM (-3)         /* device or host allocation failed */
 #define SLDG_ERR_CUDA (-4)        /* a CUDA runtime call failed */
 #define SLDG_ERR_NONFINITE (-5)   /* a reduction met NaN or Inf in f */
-#define SLDG_ERR_UNSUPPORTED (-6) /* size beyond what a kernel supports */
+#define SLDG_ERR_UNSUPPORTED (-6) /* size or mode a kernel or entry point does not support */
 #define SLDG_ERR_STATE (-7)       /* call out of order (e.g. backward before record) */
 #define SLDG_ERR_ARG (-8)         /* invalid scalar argument */
 

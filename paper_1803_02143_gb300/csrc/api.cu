@@ -821,7 +821,7 @@ const char* sldg_strerror(int code) {
     case SLDG_ERR_OOM: return "out of memory";
     case SLDG_ERR_CUDA: return "CUDA runtime error";
     case SLDG_ERR_NONFINITE: return "non-finite value in f";
-    case SLDG_ERR_UNSUPPORTED: return "size not supported by the kernels";
+    case SLDG_ERR_UNSUPPORTED: return "size or mode not supported";
     case SLDG_ERR_STATE: return "call out of order";
     case SLDG_ERR_ARG: return "invalid argument";
     default: return "unknown status";
