@@ -136,3 +136,106 @@ def test_uniform_density_has_no_field(orc, deg):
     g2 = _grid(orc, deg=2, nc=(7, 9, 2, 2), kmax=10)
     F1, _ = orc.poisson(g2, np.full(g2.xshape, 1.7))
     assert np.abs(F1).max() > 1e-4
+
+
+def _gauss_moments(a, lo, hi):
+    """Integrals of v^0, v^1, v^2 against the unit Gaussian density centred
+    at a over [lo, hi] (closed forms by the error function:
+    int u phi = -phi, int u^2 phi = Phi - u phi)."""
+    from math import erf, exp, pi, sqrt
+
+    def Phi(u):
+        return 0.5 * (1 + erf(u / sqrt(2)))
+
+    def phi(u):
+        return exp(-u * u / 2) / sqrt(2 * pi)
+
+    l, r = lo - a, hi - a
+    m0 = Phi(r) - Phi(l)
+    m1 = -(phi(r) - phi(l)) + a * m0
+    m2 = (Phi(r) - r * phi(r)) - (Phi(l) - l * phi(l)) - 2 * a * (phi(r) - phi(l)) + a * a * m0
+    return m0, m1, m2
+
+
+def _v_moments(g, f):
+    """rho and the v1^2, v2^2 moments of f at every x-node by the grid's
+    tensor Gauss-Legendre weights (nodes and weights pinned above)."""
+    F = f.reshape(g.shape)
+    w2, w3 = g.weights(2), g.weights(3)
+    v1, v2 = g.nodes(2), g.nodes(3)
+    W = np.outer(w3, w2)[:, :, None, None]
+    rho = np.sum(W * F, axis=(0, 1))
+    m11 = np.sum(W * (v1 ** 2)[None, :, None, None] * F, axis=(0, 1))
+    m22 = np.sum(W * (v2 ** 2)[:, None, None, None] * F, axis=(0, 1))
+    return rho, m11, m22
+
+
+def test_two_stream_initial_value_moments(orc):
+    # Additive two-stream initial value (kind 1) on [0, 10 pi]^2 x [-9, 9]^2:
+    #   f0 = (e^{-(v1-v0)^2/2} + e^{-(v1+v0)^2/2}) e^{-v2^2/2} / (4 pi)
+    #        * (1 + eps cos k x1 + eps cos k x2).
+    # Its v-moments are closed forms of truncated Gaussians: the density is
+    # (1 + eps cos k x1 + eps cos k x2) m0(v0) g0 with m0 the mean mass of
+    # the two shifted unit Gaussians on [-9, 9] and g0 that of the centred
+    # one; <v1^2> = 1 + v0^2 (the beams), <v2^2> = 1 (a Maxwellian).  A 4 pi
+    # / 8 pi slip, a dropped v2 factor, beams put in v2, or a product in
+    # place of the sum of the x-perturbations each fail one of these.
+    from inputs import TSI_HI, TSI_LO
+
+    g = orc.Grid(deg=3, nc=(5, 4, 24, 16), lo=TSI_LO, hi=TSI_HI, dt=0.1)
+    eps, k, v0 = 0.3, 0.2, 3.0
+    f = orc.init(g, orc.TWO_STREAM, [eps, k, v0])
+    rho, m11, m22 = _v_moments(g, f)
+    X2, X1 = np.meshgrid(g.nodes(1), g.nodes(0), indexing="ij")
+    pert = 1 + eps * np.cos(k * X1) + eps * np.cos(k * X2)
+    p, q = _gauss_moments(v0, -9, 9), _gauss_moments(-v0, -9, 9)
+    c = _gauss_moments(0.0, -9, 9)
+    beam0, beam2 = 0.5 * (p[0] + q[0]), 0.5 * (p[2] + q[2])
+    np.testing.assert_allclose(rho, pert * beam0 * c[0], rtol=2e-6)
+    np.testing.assert_allclose(m11, pert * beam2 * c[0], rtol=2e-6)
+    np.testing.assert_allclose(m22, pert * beam0 * c[2], rtol=2e-6)
+    # the oracle's own charge density agrees with this quadrature
+    np.testing.assert_allclose(orc.rho(g, f), rho, rtol=1e-13)
+
+
+def test_paper_two_stream_initial_value_moments(orc):
+    # Sec. 5, Eq. (iv-tsi) (kind 2) on [0, 10 pi]^2 x [-6, 6]^2:
+    #   f0 = (1 + eps cos k x1 cos k x2) / (8 pi) prod_d (e^{-(v_d-v0)^2/2} + e^{-(v_d+v0)^2/2}).
+    # Density (1 + eps cos k x1 cos k x2) m0^2, <v_d^2> = m2/m0 in both
+    # directions, with the truncation of the beams at |v| = 6 in m0, m2.
+    from inputs import TSI_HI
+
+    lo, hi = (0.0, 0.0, -6.0, -6.0), (TSI_HI[0], TSI_HI[1], 6.0, 6.0)
+    g = orc.Grid(deg=3, nc=(4, 5, 20, 20), lo=lo, hi=hi, dt=0.1)
+    eps, k, v0 = 0.25, 0.2, 2.4
+    f = orc.init(g, orc.TWO_STREAM_PAPER, [eps, k, v0])
+    rho, m11, m22 = _v_moments(g, f)
+    X2, X1 = np.meshgrid(g.nodes(1), g.nodes(0), indexing="ij")
+    pert = 1 + eps * np.cos(k * X1) * np.cos(k * X2)
+    p, q = _gauss_moments(v0, -6, 6), _gauss_moments(-v0, -6, 6)
+    b0, b2 = 0.5 * (p[0] + q[0]), 0.5 * (p[2] + q[2])
+    np.testing.assert_allclose(rho, pert * b0 * b0, rtol=2e-6)
+    np.testing.assert_allclose(m11, pert * b2 * b0, rtol=2e-6)
+    np.testing.assert_allclose(m22, pert * b0 * b2, rtol=2e-6)
+
+
+def test_rho_column_matches_rho(orc):
+    # The single-node v-quadrature (the checker of the full-size charge
+    # density) equals the whole-grid one at every x-node, on a grid whose
+    # two velocity directions differ in cell count, box and node count, so
+    # a swapped v1/v2 index or weight would show.
+    g = orc.Grid(deg=2, nc=(3, 4, 5, 7), lo=(0.0, 0.0, -6.0, -2.0),
+                 hi=(4 * np.pi, 2 * np.pi, 6.0, 9.0), dt=0.1)
+    f = random_f(g.shape, seed=11)
+    r = orc.rho(g, f)
+    F = f.reshape(g.shape)
+    for i1 in range(g.D(1)):
+        for i0 in range(g.D(0)):
+            c = orc.rho_column(g, F[:, :, i1, i0])
+            assert abs(c - r[i1, i0]) <= 1e-14 * max(1.0, abs(r[i1, i0]))
+    # and it weighs v1 and v2 by their own rules: a column varying in v1
+    # only against its closed form
+    v1 = g.nodes(2)
+    col = np.tile(v1 ** 2, (g.D(3), 1))
+    exact = (6.0 ** 3 - (-6.0) ** 3) / 3 * (9.0 - (-2.0))
+    assert abs(orc.rho_column(g, col) - exact) < 1e-12 * exact
