@@ -3,11 +3,14 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME] [--precision fp64|fp32]
+    python bench.py --ingest-ncu REP.ncu-rep --ncu-case NAME [--ncu-targets NAME,...]
 
 A step is one Strang step of the whole hot path (x1, x2 half drifts, rho,
 Poisson, v1, v2 kicks, x1, x2 half drifts) over the synthetic initial value
-of the workload (default: nonlinear Landau damping, 64^4 cells, degree 2,
-1.36e9 nodal values, FP64).  ``value`` is dof-updates per second over the
+of the workload (default: the two-stream instability, 64^2 x 128^2 cells,
+degree 2, 5.4e9 nodal values, FP64 storage swept in double-float
+arithmetic; the FP32-storage run and the FP64-FMA run of the same workload
+are reported beside it).  ``value`` is dof-updates per second over the
 whole job with f resident in HBM; ``e2e`` is the same metric through the C
 ABI with f uploaded from pinned host memory and W read back every step.
 With torchrun (N > 1) every rank runs an independent replica (the path
@@ -27,6 +30,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,7 +43,23 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 FP64_FMA_PER_CLK_SM = 2   # FP64 FMA units per SM of GB300 (1.25 TFLOP/s nominal)
 FP32_LANES_PER_SM = 128   # FP32 operations per clock per SM
 DF_OPS_PER_MAC = 12       # FP32 operations per lane of a double-float multiply-accumulate
-SMS = 152
+DEFAULT_WORKLOAD = "two_stream_64x128"
+
+
+def device_sms():
+    """Streaming multiprocessors of the current CUDA device."""
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def arithmetic(cfg):
+    """The arithmetic type the sweeps of a configuration compute in."""
+    if cfg.precision == "fp32":
+        return "f32"
+    if cfg.flags & 1 or cfg.flags & 16:  # FP64 FMA sweeps; the spline method sweeps in FP64
+        return "f64"
+    return "double-float (f32 pair; f64 storage)"
 
 
 def parse():
@@ -47,13 +68,19 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="nonlinear_landau_64")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true", help="skip the fp32 and adjoint lines")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     p.add_argument("--native-fp64", action="store_true",
                    help="FP64 storage swept with FP64 FMA instead of double-float arithmetic")
+    p.add_argument("--ingest-ncu", default=None, metavar="REP",
+                   help="write profiles/ncu_traffic.json from an ncu report and print its summary")
+    p.add_argument("--ncu-case", default="two_stream_64x16",
+                   help="workload the ncu report was captured on")
+    p.add_argument("--ncu-targets", default=f"{DEFAULT_WORKLOAD},nonlinear_landau_64",
+                   help="workloads (same degree and x-grid) the traffic is scaled to")
     return p.parse_args()
 
 
@@ -181,6 +208,134 @@ def committed_traffic(key):
 
 
 # ---------------------------------------------------------------------------
+# ncu report -> committed DRAM traffic per launch and a summary table
+# ---------------------------------------------------------------------------
+NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,"
+               "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed,"
+               "sm__throughput.avg.pct_of_peak_sustained_elapsed,"
+               "sm__warps_active.avg.pct_of_peak_sustained_active,"
+               "smsp__issue_active.avg.pct_of_peak_sustained_active,"
+               "sm__inst_executed.sum,launch__registers_per_thread,"
+               "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active,"
+               "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active,"
+               "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active")
+
+# translation unit of each kernel family (its sources key the traffic entry)
+KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
+                ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),
+                ("k_sweep_strided_f2", "sweep_f32.cu"), ("k_sweep_x1_f2warp", "sweep_f32.cu"),
+                ("k_rho_partial", "fields.cu"))
+
+
+def _kernel_kind(name):
+    """(kind, precision) of a sweep kernel from its ncu name, or None."""
+    prec = "fp64" if ("_df" in name or "double" in name) else "fp32"
+    if "k_sweep_x12" in name:
+        return "x12", prec
+    if "k_sweep_x1" in name:
+        return "x1", prec
+    if "k_rho_partial" in name:
+        return "rho", prec
+    m = re.search(r"k_sweep_strided_\w+<\s*\d+,\s*(\w+),\s*(\w+)", name)
+    if m:
+        periodic = m.group(1) in ("1", "true")
+        percol = m.group(2) in ("1", "true")
+        if percol and not periodic:
+            return "v", prec
+        if periodic and not percol:
+            return "x2", prec
+    return None
+
+
+def ingest_ncu(args):
+    """Per-launch DRAM traffic of the sweep kernels in an ncu report captured on
+    args.ncu_case, scaled by the ratio of nodal values to each target workload
+    (every byte of these kernels scales with the dof count), written to
+    profiles/ncu_traffic.json keyed by the current sources of each kernel's
+    translation unit; prints a markdown summary of the captured launches."""
+    import csv
+    import io
+
+    from paper_1803_02143_gb300 import configs
+
+    out = subprocess.run(["ncu", "-i", args.ingest_ncu, "--page", "raw", "--csv", "--metrics",
+                          NCU_METRICS], capture_output=True, text=True, check=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    head = rows[0]
+    data = [r for r in rows[2:] if len(r) == len(head)]
+    col = {h: i for i, h in enumerate(head)}
+    case = configs.workload(args.ncu_case)
+    by_kind, table = {}, []
+    vcount = {}
+    for r in data:
+        name = r[col["Kernel Name"]]
+        kk = _kernel_kind(name)
+
+        def num(metric):
+            v = r[col[metric]].replace(",", "") if metric in col else ""
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+
+        rd, wr = num("dram__bytes_read.sum"), num("dram__bytes_write.sum")
+        dur = num("gpu__time_duration.sum")
+        table.append((name.split("(")[0].replace("void ", "").replace("sldg::", ""), dur, rd, wr,
+                      num("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+                      num("sm__throughput.avg.pct_of_peak_sustained_elapsed"),
+                      num("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+                      num("sm__warps_active.avg.pct_of_peak_sustained_active"),
+                      num("sm__inst_executed.sum"), num("launch__registers_per_thread"),
+                      num("sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"),
+                      num("sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
+                      num("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active")))
+        if kk is None:
+            continue
+        kind, prec = kk
+        if kind == "v":  # v1 and v2 alternate within a step
+            i = vcount.get(prec, 0)
+            vcount[prec] = i + 1
+            kind = "v1" if i % 2 == 0 else "v2"
+        unit = next((u for k, u in KERNEL_UNITS if k in name), None)
+        by_kind.setdefault((prec, kind), []).append((rd + wr, unit))
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            traffic = json.load(fh)
+    except (OSError, ValueError):
+        traffic = {}
+    traffic["_note"] = ("DRAM bytes (read + write) per launch, scaled from ncu captures on a "
+                        "smaller case with the same x-grid and degree by the ratio of nodal "
+                        "values (written by bench.py --ingest-ncu); unit names the translation "
+                        "unit that instantiates the kernel and csrc_sha1 the hash of its "
+                        "sources when the counters were taken.")
+    rep = os.path.basename(args.ingest_ncu)
+    for tname in args.ncu_targets.split(","):
+        tw = configs.workload(tname)
+        scale = tw.cfg.numel / case.cfg.numel
+        for (prec, kind), vals in by_kind.items():
+            unit = vals[0][1]
+            if unit is None:
+                continue
+            b = sum(v for v, _ in vals) / len(vals)
+            traffic[f"{tname}:{prec}:{kind}"] = {
+                "bytes_per_launch": b * scale, "capture": f"{rep} on {case.name}",
+                "csrc_sha1": unit_sha1(unit), "unit": unit}
+    with open(path, "w") as fh:
+        json.dump(traffic, fh, indent=1, sort_keys=True)
+    n = case.cfg.numel
+    print(f"Captured on {case.name}: {n} nodal values; algorithmic bytes per sweep launch "
+          f"2 e N (e = element size; the fused x pass does two sweeps per launch).\n")
+    print("| kernel | ms | DRAM read GB | DRAM write GB | DRAM % | SM % | issue active % | "
+          "warps active % | warp instr per dof | regs | FMA pipe % | ALU pipe % | FP64 pipe % |")
+    print("|---|---|---|---|---|---|---|---|---|---|---|---|---|")
+    for t in table:
+        print(f"| `{t[0]}` | {t[1] / 1e6:.3f} | {t[2] / 1e9:.3f} | {t[3] / 1e9:.3f} | {t[4]:.1f} "
+              f"| {t[5]:.1f} | {t[6]:.1f} | {t[7]:.1f} | {t[8] / n:.2f} | {t[9]:.0f} | "
+              f"{t[10]:.1f} | {t[11]:.1f} | {t[12]:.1f} |")
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle baseline on a bounded slab of the workload
 # ---------------------------------------------------------------------------
 def oracle_slab(w, vcells=32):
@@ -208,7 +363,10 @@ def time_oracle(w, nsteps, warmup=0):
     return {"value": dofs * nsteps / dt, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
             "sample": (f"{nsteps} Strang step(s) of the FP64 oracle on {g.nc[0]}x{g.nc[1]}x"
                        f"{g.nc[2]}x{g.nc[3]} cells, degree {g.deg} ({dofs} dofs; the workload's "
-                       f"x-grid with a reduced v-grid), {dt:.1f} s"),
+                       f"x-grid, degree and domain with a reduced v-grid), {dt:.1f} s"),
+            "extrapolated": (f"per-dof rate of the slab taken for the workload's "
+                             f"{w.cfg.numel} dofs (same line lengths along x, same degree)"
+                             if dofs != w.cfg.numel else None),
             "seconds": dt, "dofs": dofs}
 
 
@@ -256,10 +414,14 @@ def run_reference(args, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "oracle_sample": list(g.nc), "degree": g.deg},
+        "config": {"workload": w.name, "oracle_sample": list(g.nc), "degree": g.deg,
+                   "storage": "fp64", "arithmetic": "f64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
                          "sample": f"{args.steps} steps on {g.nc} cells, degree {g.deg} "
-                                   f"({f.size} dofs), host {cpu_info()}"},
+                                   f"({f.size} dofs), host {cpu_info()}",
+                         "extrapolated": (f"per-dof rate of the slab taken for the workload's "
+                                          f"{w.cfg.numel} dofs" if f.size != w.cfg.numel
+                                          else None)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -268,7 +430,7 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def sweep_roofline(w, timing, steps_timed, pk, peak_src):
+def sweep_roofline(w, timing, steps_timed, pk, peak_src, sms):
     """Dominant kernel class of the timed region, against its roofline."""
     cfg = w.cfg
     n = cfg.n
@@ -294,12 +456,12 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
         # bound is the roofline with the longer floor for this launch.
         sweeps_per_launch = 2 if kind == "x12" else 1
         ops = sweeps_per_launch * cfg.numel * (2 * n) * DF_OPS_PER_MAC
-        peak_t = SMS * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+        peak_t = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
         if ops / (peak_t * 1e12) > algo_bytes / (pk["hbm_gbs"] * 1e9):
             return {"bound": "alu", "achieved": ops / avg_s / 1e12, "peak": peak_t,
                     "unit": "T FP32 ops/s", "frac": ops / avg_s / 1e12 / peak_t,
                     "traffic": traffic, "kernel": f"sweep_{kind}",
-                    "peak_source": "FP32 lanes x max SM clock (152 SMs x 128 lanes)",
+                    "peak_source": f"FP32 lanes x max SM clock ({sms} SMs x 128 lanes)",
                     "hbm": hbm, "avg_launch_ms": ms / cnt, "per_kernel_ms_per_step": per_kernel}
     if cfg.precision == "fp64" and spline:
         # cubic-spline sweeps in FP64 arithmetic: per point one FMA in each of
@@ -307,11 +469,11 @@ def sweep_roofline(w, timing, steps_timed, pk, peak_src):
         algo_flops = 2 * 6 * cfg.numel
         native = True
     if cfg.precision == "fp64" and native:
-        peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
+        peak_tf = sms * FP64_FMA_PER_CLK_SM * 2 * clk * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": algo_flops / avg_s / 1e12, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": algo_flops / avg_s / 1e12 / peak_tf,
                 "traffic": traffic, "kernel": f"sweep_{kind}",
-                "peak_source": "FP64 FMA units x max SM clock (152 SMs x 2 FMA x 2 flop)",
+                "peak_source": f"FP64 FMA units x max SM clock ({sms} SMs x 2 FMA x 2 flop)",
                 "hbm": hbm}
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -329,17 +491,19 @@ def run_forward(w, steps, warmup, world, local, sample_clocks=True):
 
     s = Sldg(w.cfg)
     s.set_initial(w.kind, w.params)
-    s.step(warmup)
+    W0 = s.step(warmup, history=True)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if sample_clocks else None
     barrier(world)
     torch.cuda.synchronize()
+    # CUDA events around every kernel launch on the context's stream, inside
+    # the timed region (the steps then run as eager launches)
     s.timing(True)
     n0 = s.launch_count
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s.stream)
-    s.step(steps)
+    W1 = s.step(steps, history=True)  # W of every step to a device slot, one read at the end
     e1.record(s.stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -348,29 +512,63 @@ def run_forward(w, steps, warmup, world, local, sample_clocks=True):
     launches = s.launch_count - n0
     s.timing(False)
     ck = clocks.stop() if clocks else None
-    return s, ms, timing, launches, ck
+    return s, ms, timing, launches, ck, np.concatenate([W0, W1])
 
 
 def run_splitting_variants(args, w, flags, local):
     """Step time of the same workload and precision with merged drifts (one x
     pass per step instead of two) and with the order-4 triple jump (three
-    Strang sub-steps per step), merged or not."""
+    Strang sub-steps per step), merged or not (a few steps each)."""
+    import torch
+
     from paper_1803_02143_gb300 import _native as N
     from paper_1803_02143_gb300 import configs
 
     out = {}
+    steps = max(2, min(args.steps, 5))
     for name, fl in (("strang_merged", N.SLDG_FLAG_MERGE_DRIFTS), ("order4", N.SLDG_FLAG_ORDER4),
                      ("order4_merged", N.SLDG_FLAG_ORDER4 | N.SLDG_FLAG_MERGE_DRIFTS)):
         w3 = configs.workload(args.workload, w.cfg.precision, flags | fl)
-        s3, ms3, _, _, _ = run_forward(w3, args.steps, args.warmup, 1, local, sample_clocks=False)
+        s3, ms3, _, _, _, _ = run_forward(w3, steps, 1, 1, local, sample_clocks=False)
         s3.close()
         del s3
-        import torch
-
         torch.cuda.empty_cache()
-        out[name] = {"ms_per_step": ms3 / args.steps,
-                     "value": w3.cfg.numel * args.steps / (ms3 / 1e3), "unit": UNIT}
+        out[name] = {"ms_per_step": ms3 / steps, "steps": steps,
+                     "value": w3.cfg.numel * steps / (ms3 / 1e3), "unit": UNIT}
     return out
+
+
+def w_error(W, Wref, dt, t0_step=1):
+    """FP32 against FP64: the largest difference of the electric-energy
+    histories relative to the largest |W| of the reference, and the
+    relative difference at each step with its time."""
+    W, Wref = np.asarray(W), np.asarray(Wref)
+    rel = np.abs(W - Wref) / np.maximum(np.abs(Wref), 1e-300)
+    return {"W_max_rel": float(np.abs(W - Wref).max() / np.abs(Wref).max()),
+            "steps": int(W.size),
+            "t": [round(dt * (t0_step + m), 6) for m in range(W.size)],
+            "W_rel_per_step": [float(x) for x in rel]}
+
+
+def run_variant(args, name, prec, flags, local, pk, pk_src, sms, steps=None, warmup=None):
+    """One more workload or storage precision, timed like the headline run;
+    returns its line entry and its W history."""
+    import torch
+
+    from paper_1803_02143_gb300 import configs
+
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    w2 = configs.workload(name, prec, flags)
+    s2, ms2, t2, _, _, W2 = run_forward(w2, steps, warmup, 1, local, sample_clocks=False)
+    s2.close()
+    del s2
+    torch.cuda.empty_cache()
+    entry = {"workload": w2.name, "dtype": arithmetic(w2.cfg), "dofs": w2.cfg.numel,
+             "value": w2.cfg.numel * steps / (ms2 / 1e3), "unit": UNIT,
+             "ms_per_step": ms2 / steps, "steps": steps,
+             "roofline": sweep_roofline(w2, t2, steps, pk, pk_src, sms)}
+    return entry, W2
 
 
 def run_e2e(s, w, steps):
@@ -444,42 +642,58 @@ def run_ours(args, world, rank, local):
     flags = 1 if args.native_fp64 else 0
     w = configs.workload(args.workload, args.precision, flags)
     pk, pk_src = peaks()
-    s, ms, timing, launches, clocks = run_forward(w, args.steps, args.warmup, world, local)
+    sms = device_sms()
+    s, ms, timing, launches, clocks, W = run_forward(w, args.steps, args.warmup, world, local)
     ms_max = max_over_ranks(ms, world)
     value = job_value(w.cfg.numel, args.steps, world, ms_max)
-    roof = sweep_roofline(w, timing, args.steps, pk, pk_src)
+    roof = sweep_roofline(w, timing, args.steps, pk, pk_src, sms)
     e2e = None
     if not args.no_e2e:
         barrier(world)
-        e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
-        ms_e2e = max_over_ranks(e2e["ms_per_step"] * e2e["steps"], world)
-        e2e["value"] = job_value(w.cfg.numel, e2e["steps"], world, ms_e2e)
-        e2e["ms_per_step"] = ms_e2e / e2e["steps"]
+        try:
+            e2e = run_e2e(s, w, max(3, min(args.steps, 10)))
+            ms_e2e = max_over_ranks(e2e["ms_per_step"] * e2e["steps"], world)
+            e2e["value"] = job_value(w.cfg.numel, e2e["steps"], world, ms_e2e)
+            e2e["ms_per_step"] = ms_e2e / e2e["steps"]
+        except (RuntimeError, MemoryError) as exc:  # pinned host memory for f not available
+            e2e = {"value": None, "unit": UNIT, "error": str(exc).splitlines()[0][:200]}
     s.close()
     del s
     torch.cuda.empty_cache()
     extras = {}
     if not args.no_extras and rank == 0:
-        # the other storage precision, and FP64 storage with FP64-FMA sweeps
-        variants = [("fp32", "fp32", 0), ("fp64_fma", "fp64", 1)]
-        if w.cfg.precision == "fp32":
-            variants = [("fp64", "fp64", 0)]
         times = {}
-        for name, prec, fl in variants:
-            w2 = configs.workload(args.workload, prec, fl)
-            s2, ms2, t2, _, _ = run_forward(w2, args.steps, args.warmup, 1, local,
-                                            sample_clocks=False)
-            s2.close()
-            del s2
-            torch.cuda.empty_cache()
-            times[name] = ms2
-            extras[name] = {"value": w2.cfg.numel * args.steps / (ms2 / 1e3), "unit": UNIT,
-                            "ms_per_step": ms2 / args.steps,
-                            "roofline": sweep_roofline(w2, t2, args.steps, pk, pk_src)}
-        if "fp32" in times:
-            extras["fp32_over_fp64_step_time"] = times["fp32"] / ms
-        elif "fp64" in times:
-            extras["fp32_over_fp64_step_time"] = ms / times["fp64"]
+        if w.cfg.precision == "fp64" and not flags:
+            # FP32 storage of the same workload, with its W history against
+            # this run's; FP64 storage swept with FP64 FMA
+            e32, W32 = run_variant(args, w.name, "fp32", 0, local, pk, pk_src, sms)
+            e32["error_vs_fp64"] = w_error(W32, W, w.cfg.dt)
+            extras["fp32"] = e32
+            times["fp32"] = e32["ms_per_step"]
+            efma, Wfma = run_variant(args, w.name, "fp64", 1, local, pk, pk_src, sms,
+                                     steps=max(2, min(args.steps, 10)), warmup=1)
+            n = min(len(Wfma), len(W))
+            efma["double_float_vs_fp64_fma"] = {
+                "W_max_rel": float(np.abs(W[:n] - Wfma[:n]).max() / np.abs(Wfma[:n]).max()),
+                "steps": n}
+            extras["fp64_fma"] = efma
+            extras["fp32_over_fp64_step_time"] = times["fp32"] / (ms / args.steps)
+        elif w.cfg.precision == "fp32":
+            e64, W64 = run_variant(args, w.name, "fp64", 0, local, pk, pk_src, sms)
+            extras["fp64"] = e64
+            extras["error_vs_fp64"] = w_error(W, W64, w.cfg.dt)
+            extras["fp32_over_fp64_step_time"] = (ms / args.steps) / e64["ms_per_step"]
+        # the large mixed-precision workload (128^4 cells, degree 1, FP32
+        # storage) and its FP64-storage twin
+        if w.name != "mixed_landau_128":
+            m32, Wm32 = run_variant(args, "mixed_landau_128", "fp32", 0, local, pk, pk_src, sms)
+            m64, Wm64 = run_variant(args, "mixed_landau_128", "fp64", 0, local, pk, pk_src, sms)
+            m32["error_vs_fp64"] = w_error(Wm32, Wm64, configs.workload("mixed_landau_128").cfg.dt)
+            m32["error_vs_fp64"].pop("W_rel_per_step")
+            m32["error_vs_fp64"].pop("t")
+            m32["fp64_storage"] = {k: m64[k] for k in ("dtype", "value", "unit", "ms_per_step")}
+            m32["fp32_over_fp64_step_time"] = m32["ms_per_step"] / m64["ms_per_step"]
+            extras["mixed_landau_128"] = m32
         extras["adjoint"] = run_adjoint_ratio()
         extras["splitting"] = run_splitting_variants(args, w, flags, local)
     cpu = None
@@ -491,18 +705,16 @@ def run_ours(args, world, rank, local):
         cpu["host"] = cpu_info()
     if rank != 0:
         return
+    fb = w.cfg.numel * (8 if w.cfg.precision == "fp64" else 4)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w.cfg.precision == "fp64" else "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": arithmetic(w.cfg), "data": "synthetic",
         "config": {"workload": w.name, "cells": list(w.cfg.ncell), "degree": w.cfg.degree,
-                   "fp64_sweeps": ("fp64 fma" if w.cfg.flags else "double-float on the fp32 pipe")
-                   if w.cfg.precision == "fp64" else None,
+                   "storage": w.cfg.precision, "arithmetic": arithmetic(w.cfg),
                    "dofs": w.cfg.numel, "dt": w.cfg.dt, "initial": list(w.params),
-                   "l2": "inputs larger than L2 (f is %.1f GB)" % (
-                       w.cfg.numel * (8 if w.cfg.precision == "fp64" else 4) / 1e9),
-                   "parallelism": f"replicas x{world}"},
+                   "l2": "inputs larger than L2 (f is %.1f GB), no flush" % (fb / 1e9),
+                   "parallelism": f"replicas x{world}", "sms": sms},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -512,6 +724,9 @@ def run_ours(args, world, rank, local):
 
 def main():
     args = parse()
+    if args.ingest_ncu:
+        ingest_ncu(args)
+        return
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)

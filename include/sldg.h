@@ -222,6 +222,14 @@ int sldg_step_host_batches(sldg_ctx* ctx, const void* host_f, long long batch_st
  * Errors: ARG (dim outside 0..3), STATE (v-sweep before any field). */
 int sldg_sweep(sldg_ctx* ctx, int dim, double frac);
 
+/* The free-streaming half of a Strang step on its own (Sec. 2, e^{tau A} =
+ * e^{tau A2} e^{tau A1}): X1 then X2 in place on f, each line shifted by its
+ * velocity node times dt * frac, periodic in x.  These are the kernels and
+ * the launch configuration of the drifts inside sldg_step (one fused pass
+ * over each x-plane where the layout allows it, else the two sweeps), with
+ * IEEE values in and out.  Errors: ARG (frac not finite), CUDA. */
+int sldg_drift(sldg_ctx* ctx, double frac);
+
 /* rho = Q f (v-quadrature, Sec. 2: rho = int g dv) and E = L rho (spectral
  * Poisson, Sec. 3 "FFTW"; dense map on the nodes with the mean mode removed)
  * of the current f; stores them in the context. */
@@ -261,8 +269,15 @@ int sldg_sweep_adjoint(sldg_ctx* ctx, int dim, double frac, void* lam, const voi
  * SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE), CUDA. */
 int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
 
+/* J = sum_m c_m W(E^m) of the last sldg_record, c_m = cW[m] (host, ncW =
+ * nsteps doubles) or dt if cW is NULL: the time-integrated electric energy
+ * for c_m = dt (a compensated sum of the recorded W history), to *J_out.
+ * Synchronises.  Errors: BAD_PTR, STATE (no record), ARG (ncW differs from
+ * the recorded step count), CUDA. */
+int sldg_objective(sldg_ctx* ctx, const double* cW, int ncW, double* J_out);
+
 /* Reverse pass of the last sldg_record: gradient of
- *   J = sum_m c_m W(E^m),   c_m = cW[m] (host, nsteps doubles) or dt if NULL,
+ *   J = sum_m c_m W(E^m),   c_m = cW[m] (host, ncW = nsteps doubles) or dt if NULL,
  * (the time-integrated electric energy for c_m = dt) with respect to every
  * nodal value of the recorded initial f, written to grad (device, N elements
  * of the context precision).  J_out (host, nullable) receives J.  f is left
@@ -278,10 +293,10 @@ int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
  * log2(ckpt_every) times; with one slot, from the checkpoint for every
  * step.  The gradient is the same whatever the number of slots (the same
  * arithmetic, only repeated).
- * Errors: STATE (no record), BAD_PTR, OOM (not even one slot fits),
- * UNSUPPORTED (SLDG_FLAG_ORDER4, SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE),
- * CUDA. */
-int sldg_backward(sldg_ctx* ctx, const double* cW, void* grad, double* J_out);
+ * Errors: STATE (no record), BAD_PTR, ARG (ncW differs from the recorded
+ * step count), OOM (not even one slot fits), UNSUPPORTED (SLDG_FLAG_ORDER4,
+ * SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE), CUDA. */
+int sldg_backward(sldg_ctx* ctx, const double* cW, int ncW, void* grad, double* J_out);
 
 /* Upper bound on the recomputation slots of sldg_backward (0 = as many as a
  * segment can use and the device has room for).  Errors: BAD_PTR, ARG. */
@@ -319,13 +334,23 @@ int sldg_initial_param_grad(sldg_ctx* ctx, int kind, const double* params, int n
  * it reads it and overwrites all of rho_dev.  Every call reuses the same
  * array, so calls that overlap on the GPU (other streams, other host
  * threads) race and must be ordered by the caller.
- * Errors: BAD_PTR, BAD_CONFIG, UNSUPPORTED (x-plane D_0 D_1 above 2^19
- * nodes, or a v-chunk beyond shared memory), CUDA. */
+ * A CUDA error left pending by the caller's earlier work is cleared on
+ * entry (it would otherwise read as this call's launch failure).
+ * Errors: BAD_PTR, BAD_CONFIG (every configuration sldg_init rejects),
+ * UNSUPPORTED (x-plane D_0 D_1 above 2^19 nodes, or a v-chunk beyond shared
+ * memory), CUDA. */
 int sldg_rho_noalloc(const sldg_config* cfg, const void* f_dev, double* rho_dev, void* stream);
 
 /* ---- measurement ---------------------------------------------------------------
  * Kernel launches issued by this context since init (all entry points). */
 long long sldg_launch_count(const sldg_ctx* ctx);
+
+/* Launch shape of the last fused X1 X2 pass this context ran (either pointer
+ * nullable): the CTAs that share one x-plane (a thread-block cluster) and
+ * the lanes given to each pair of x1 lines in its X1 phase (32: whole warps;
+ * fewer: several line pairs per warp).  Both 0 before the first fused pass.
+ * Errors: BAD_PTR. */
+int sldg_x_pass_shape(const sldg_ctx* ctx, int* cluster_ctas, int* lanes_per_line_pair);
 
 /* enable != 0: bracket every subsequent kernel launch with CUDA events on the
  * context's stream, accumulated per kernel class SLDG_K_*; 0 stops; both

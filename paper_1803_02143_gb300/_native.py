@@ -92,18 +92,21 @@ SIGNATURES = {
     "sldg_step": (ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     "sldg_step_host_batches": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, ctypes.c_int, _DP]),
     "sldg_sweep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double]),
+    "sldg_drift": (ctypes.c_int, [_VP, ctypes.c_double]),
     "sldg_compute_fields": (ctypes.c_int, [_VP]),
     "sldg_set_field": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "sldg_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
     "sldg_diagnostics": (ctypes.c_int, [_VP, ctypes.POINTER(sldg_diag)]),
     "sldg_sweep_adjoint": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP]),
     "sldg_record": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _DP]),
-    "sldg_backward": (ctypes.c_int, [_VP, _DP, _VP, _DP]),
+    "sldg_objective": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _DP]),
+    "sldg_backward": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _VP, _DP]),
     "sldg_set_slot_limit": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sldg_backward_stats": (ctypes.c_int, [_VP, _LLP, ctypes.POINTER(ctypes.c_int)]),
     "sldg_initial_param_grad": (ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.c_int, _VP, _DP]),
     "sldg_rho_noalloc": (ctypes.c_int, [ctypes.POINTER(sldg_config), _VP, _VP, _VP]),
     "sldg_launch_count": (ctypes.c_longlong, [_VP]),
+    "sldg_x_pass_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sldg_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sldg_timing_read": (ctypes.c_int, [_VP, _DP, _LLP]),
 }
@@ -186,6 +189,10 @@ def sldg_sweep(ctx, dim: int, frac: float) -> None:
     _check("sldg_sweep", load().sldg_sweep(ctx, int(dim), float(frac)))
 
 
+def sldg_drift(ctx, frac: float) -> None:
+    _check("sldg_drift", load().sldg_drift(ctx, float(frac)))
+
+
 def sldg_compute_fields(ctx) -> None:
     _check("sldg_compute_fields", load().sldg_compute_fields(ctx))
 
@@ -220,9 +227,17 @@ def sldg_record(ctx, nsteps: int, ckpt_every: int, W_history=None) -> None:
     _check("sldg_record", load().sldg_record(ctx, int(nsteps), int(ckpt_every), _dptr(W_history)))
 
 
+def sldg_objective(ctx, cW=None) -> float:
+    J = ctypes.c_double(0.0)
+    n = 0 if cW is None else int(cW.size)
+    _check("sldg_objective", load().sldg_objective(ctx, _dptr(cW), n, ctypes.byref(J)))
+    return J.value
+
+
 def sldg_backward(ctx, cW, grad_ptr: int) -> float:
     J = ctypes.c_double(0.0)
-    _check("sldg_backward", load().sldg_backward(ctx, _dptr(cW), _VP(grad_ptr), ctypes.byref(J)))
+    n = 0 if cW is None else int(cW.size)
+    _check("sldg_backward", load().sldg_backward(ctx, _dptr(cW), n, _VP(grad_ptr), ctypes.byref(J)))
     return J.value
 
 
@@ -255,6 +270,13 @@ def sldg_rho_noalloc(cfg: sldg_config, f_ptr: int, rho_ptr: int, stream_ptr: int
 
 def sldg_launch_count(ctx) -> int:
     return load().sldg_launch_count(ctx)
+
+
+def sldg_x_pass_shape(ctx):
+    cs = ctypes.c_int(0)
+    lanes = ctypes.c_int(0)
+    _check("sldg_x_pass_shape", load().sldg_x_pass_shape(ctx, ctypes.byref(cs), ctypes.byref(lanes)))
+    return cs.value, lanes.value
 
 
 def sldg_timing(ctx, enable: bool) -> None:

@@ -55,6 +55,13 @@ WORKLOADS = {
         "two_stream_64x128",
         Config(degree=2, ncell=(64, 64, 128, 128), lo=TSI_LO, hi=TSI_HI, dt=0.05),
         N.SLDG_INIT_TWO_STREAM, (1e-3, 0.2, 3.0), 800),
+    # the two-stream workload's x-grid (64^2 cells, degree 2: the same x-planes
+    # and x-lines) with 16^2 v-cells (8.5e7 dofs, 0.68 GB FP64, larger than
+    # L2) for profiling captures
+    "two_stream_64x16": Workload(
+        "two_stream_64x16",
+        Config(degree=2, ncell=(64, 64, 16, 16), lo=TSI_LO, hi=TSI_HI, dt=0.05),
+        N.SLDG_INIT_TWO_STREAM, (1e-3, 0.2, 3.0), 800),
     # the paper's dG4 (degree 3) runs of Sec. 4 and Table 1: nonlinear Landau
     # damping, dt 0.1 to T = 50, at 64, 128 and 144 nodal values per direction
     "landau_dg4_16": Workload("landau_dg4_16", _landau(3, 16, 0.1, 0.5), N.SLDG_INIT_LANDAU,

@@ -135,30 +135,6 @@ double node_weight(const sldg_ctx* c, int d, long long i) {
   return c->g.h[d] * c->basis.w[i % c->g.n];
 }
 
-int validate(const sldg_config* cfg) {
-  if (cfg->degree < 0 || cfg->degree > 3) return SLDG_ERR_BAD_CONFIG;
-  for (int d = 0; d < 4; ++d) {
-    if (cfg->ncell[d] < 2) return SLDG_ERR_BAD_CONFIG;
-    if (!(cfg->hi[d] > cfg->lo[d]) || !std::isfinite(cfg->hi[d]) || !std::isfinite(cfg->lo[d]))
-      return SLDG_ERR_BAD_CONFIG;
-  }
-  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION | SLDG_FLAG_ORDER4 |
-                     SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
-    return SLDG_ERR_BAD_CONFIG;
-  if (cfg->flags & SLDG_FLAG_SPLINE) {
-    // a spline sweep stages two [n][33] tiles of a line direction on chip
-    const long long esize = cfg->precision == SLDG_FP64 ? 8 : 4;
-    if (cfg->degree != 0 || cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
-    for (int d = 0; d < 4; ++d)
-      if (cfg->ncell[d] < 3 || 2LL * cfg->ncell[d] * 33 * esize > 227 * 1024)
-        return SLDG_ERR_BAD_CONFIG;
-  }
-  return SLDG_OK;
-}
-
 int x1_lines_per_tile(const sldg_ctx* c) {
   const long long D0 = c->g.D[0], D1 = c->g.D[1];
   int best = 1;
@@ -479,10 +455,10 @@ int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* 
   const cudaError_t e =
       c->prec == SLDG_FP32
           ? launch_sweep_x12_f32(buf, c->g, trans ? m0->abt : m0->ab, s0,
-                                 trans ? m1->abt : m1->ab, s1, c->stream)
+                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape)
           : launch_sweep_x12_df(buf, c->g, trans ? m0->abt2 : m0->ab2, s0,
                                 trans ? m1->abt2 : m1->ab2, s1, in_df ? 1 : 0, out_df ? 1 : 0,
-                                c->stream);
+                                c->stream, c->x12_shape);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -811,6 +787,31 @@ int build_tables(sldg_ctx* c) {
 // =============================================================================
 // C ABI
 // =============================================================================
+// The checks of sldg_init (every entry point that takes a configuration).
+int sldg::validate_config(const sldg_config* cfg) {
+  if (cfg->degree < 0 || cfg->degree > 3) return SLDG_ERR_BAD_CONFIG;
+  for (int d = 0; d < 4; ++d) {
+    if (cfg->ncell[d] < 2) return SLDG_ERR_BAD_CONFIG;
+    if (!(cfg->hi[d] > cfg->lo[d]) || !std::isfinite(cfg->hi[d]) || !std::isfinite(cfg->lo[d]))
+      return SLDG_ERR_BAD_CONFIG;
+  }
+  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->vbc != SLDG_VBC_ZERO_INFLOW && cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & ~(SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_NO_XFUSION | SLDG_FLAG_ORDER4 |
+                     SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
+    return SLDG_ERR_BAD_CONFIG;
+  if (cfg->flags & SLDG_FLAG_SPLINE) {
+    // a spline sweep stages two [n][33] tiles of a line direction on chip
+    const long long esize = cfg->precision == SLDG_FP64 ? 8 : 4;
+    if (cfg->degree != 0 || cfg->vbc != SLDG_VBC_PERIODIC) return SLDG_ERR_BAD_CONFIG;
+    for (int d = 0; d < 4; ++d)
+      if (cfg->ncell[d] < 3 || 2LL * cfg->ncell[d] * 33 * esize > 227 * 1024)
+        return SLDG_ERR_BAD_CONFIG;
+  }
+  return SLDG_OK;
+}
+
 extern "C" {
 
 const char* sldg_strerror(int code) {
@@ -828,12 +829,12 @@ const char* sldg_strerror(int code) {
   }
 }
 
-int sldg_abi_version(void) { return 1; }
+int sldg_abi_version(void) { return 2; }
 
 int sldg_init(const sldg_config* cfg, void* f_dev, void* stream, sldg_ctx** out) {
   if (!cfg || !out) return SLDG_ERR_BAD_PTR;
   *out = nullptr;
-  int rc = validate(cfg);
+  int rc = validate_config(cfg);
   if (rc != SLDG_OK) return rc;
   if (!f_dev || (reinterpret_cast<uintptr_t>(f_dev) & 15)) return SLDG_ERR_BAD_PTR;
   sldg_ctx* c = new (std::nothrow) sldg_ctx();
@@ -1044,6 +1045,12 @@ int sldg_sweep(sldg_ctx* c, int dim, double frac) {
   if (!c) return SLDG_ERR_BAD_PTR;
   if (dim < 0 || dim > 3 || !std::isfinite(frac)) return SLDG_ERR_ARG;
   return run_sweep(c, c->f, dim, frac, false, nullptr, nullptr);
+}
+
+int sldg_drift(sldg_ctx* c, double frac) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (!std::isfinite(frac)) return SLDG_ERR_ARG;
+  return drift(c, c->f, frac, false, false);
 }
 
 int sldg_compute_fields(sldg_ctx* c) {
@@ -1323,29 +1330,43 @@ int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>
 
 extern "C" {
 
-int sldg_backward(sldg_ctx* c, const double* cW, void* grad, double* J_out) {
+// J = sum_m c_m W_m of the last recording, c_m = cW[m] or dt: a compensated
+// (Neumaier) sum on the host of the recorded W history
+static int recorded_objective(sldg_ctx* c, const double* cW, double* J) {
+  const int n = c->rec_nsteps;
+  std::vector<double> W(n);
+  SLDG_CU(cudaMemcpyAsync(W.data(), c->d_Wrec, n * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  SLDG_CU(cudaStreamSynchronize(c->stream));
+  double s = 0.0, comp = 0.0;
+  for (int m = 0; m < n; ++m) {
+    const double x = (cW ? cW[m] : c->g.dt) * W[m];
+    const double t = s + x;
+    comp += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  *J = s + comp;
+  return SLDG_OK;
+}
+
+int sldg_objective(sldg_ctx* c, const double* cW, int ncW, double* J_out) {
+  if (!c || !J_out) return SLDG_ERR_BAD_PTR;
+  if (!c->recorded) return SLDG_ERR_STATE;
+  if (cW && ncW != c->rec_nsteps) return SLDG_ERR_ARG;
+  return recorded_objective(c, cW, J_out);
+}
+
+int sldg_backward(sldg_ctx* c, const double* cW, int ncW, void* grad, double* J_out) {
   if (!c || !grad) return SLDG_ERR_BAD_PTR;
   if (c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE))
     return SLDG_ERR_UNSUPPORTED;
   if (!c->recorded) return SLDG_ERR_STATE;
+  if (cW && ncW != c->rec_nsteps) return SLDG_ERR_ARG;
   const Grid& g = c->g;
   const int n = c->rec_nsteps, ck = c->rec_ckpt;
   const size_t fb = g.N * c->esize;
   char* pool = reinterpret_cast<char*>(c->d_ckpool);
-  // J from the recorded W history (compensated host sum)
-  if (J_out) {
-    std::vector<double> W(n);
-    SLDG_CU(cudaMemcpyAsync(W.data(), c->d_Wrec, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    SLDG_CU(cudaStreamSynchronize(c->stream));
-    double s = 0.0, comp = 0.0;
-    for (int m = 0; m < n; ++m) {
-      const double x = (cW ? cW[m] : g.dt) * W[m];
-      const double t = s + x;
-      comp += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
-      s = t;
-    }
-    *J_out = s + comp;
-  }
+  if (J_out) SLDG_TRY(recorded_objective(c, cW, J_out));
   // working memory: g2, g3 and the recomputation slots (as many as a segment
   // can use, within the free device memory and the slot limit)
   for (int i = 0; i < 2; ++i)
@@ -1415,6 +1436,13 @@ int sldg_initial_param_grad(sldg_ctx* c, int kind, const double* params, int npa
 
 // ---- measurement ----------------------------------------------------------------------
 long long sldg_launch_count(const sldg_ctx* c) { return c ? c->launches : 0; }
+
+int sldg_x_pass_shape(const sldg_ctx* c, int* cluster_ctas, int* lanes_per_line_pair) {
+  if (!c) return SLDG_ERR_BAD_PTR;
+  if (cluster_ctas) *cluster_ctas = c->x12_shape[0];
+  if (lanes_per_line_pair) *lanes_per_line_pair = c->x12_shape[1];
+  return SLDG_OK;
+}
 
 int sldg_timing(sldg_ctx* c, int enable) {
   if (!c) return SLDG_ERR_BAD_PTR;

@@ -72,15 +72,20 @@ cudaError_t launch_spline_shifts(int prec, long long count, const double* src, d
 // adjoint before the sweep, a.g = the forward input, a.dab2, a.s, a.epart)
 cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
-// fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the layout does not fit
+// fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the
+// layout does not fit.  shape (nullable, two ints): the launch's CTAs per
+// x-plane (cluster size) and lanes per x1 line pair of its X1 phase.
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
-                                 const void* ab2, const int* s2, cudaStream_t st);
+                                 const void* ab2, const int* s2, cudaStream_t st,
+                                 int* shape = nullptr);
 // the same for FP64 storage in double-float arithmetic (sweep_df.cu); ab1, ab2
 // are the (hi, lo) float-pair tables, in_df / out_df the element formats
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
-                                cudaStream_t st);
+                                cudaStream_t st, int* shape = nullptr);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
+// SLDG_OK or SLDG_ERR_BAD_CONFIG: the configuration checks of sldg_init (api.cu)
+int validate_config(const sldg_config* cfg);
 
 }  // namespace sldg
 
@@ -177,6 +182,7 @@ struct sldg_ctx {
   double t = 0.0;
   long long step = 0;
   long long launches = 0;
+  int x12_shape[2] = {0, 0};  // last fused x pass: CTAs per x-plane, lanes per x1 line pair
 
   // timing
   bool timing = false;

@@ -628,7 +628,17 @@ cudaError_t launch_energy(const double* E1, const double* E2, const double* wx, 
   return cudaGetLastError();
 }
 
-static int reduce_blocks() { return 4 * 152; }
+// Grid-stride kernels and two-stage reductions: four blocks per SM of the
+// current device (the same count at allocation and at launch).
+static int reduce_blocks() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;  // GB300
+  }
+  return 4 * sms;
+}
 
 size_t diag_scratch_doubles() { return (size_t)reduce_blocks() * 8 + 8; }
 

@@ -99,10 +99,8 @@ extern "C" int sldg_rho_noalloc(const sldg_config* cfg, const void* f_dev, doubl
                                 void* stream) {
   using namespace sldg;
   if (!cfg || !f_dev || !rho_dev) return SLDG_ERR_BAD_PTR;
-  if (cfg->degree < 0 || cfg->degree > 3) return SLDG_ERR_BAD_CONFIG;
-  if (cfg->precision != SLDG_FP64 && cfg->precision != SLDG_FP32) return SLDG_ERR_BAD_CONFIG;
-  for (int d = 0; d < 4; ++d)
-    if (cfg->ncell[d] < 2 || !(cfg->hi[d] > cfg->lo[d])) return SLDG_ERR_BAD_CONFIG;
+  // the configurations sldg_init accepts, and only those
+  if (validate_config(cfg) != SLDG_OK) return SLDG_ERR_BAD_CONFIG;
   const int n = cfg->degree + 1;
   VQuad q;
   q.n = n;
@@ -114,6 +112,9 @@ extern "C" int sldg_rho_noalloc(const sldg_config* cfg, const void* f_dev, doubl
   const long long Dv = q.D2 * cfg->ncell[3] * n;
   if (Dx > kScratchDoubles) return SLDG_ERR_UNSUPPORTED;  // x-plane beyond the fixed scratch
 
+  // An error left pending by the caller's earlier work would otherwise be
+  // reported as this call's launch failure: clear it first.
+  cudaGetLastError();
   // One-time set-up per device: the device address of the scratch array.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -158,7 +159,11 @@ extern "C" int sldg_rho_noalloc(const sldg_config* cfg, const void* f_dev, doubl
       k_rho_partial_noalloc<float><<<grid, kThreads, smem, st>>>(
           static_cast<const float*>(f_dev), Dx, Dv, chunk, q, scratch);
   }
-  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SLDG_ERR_CUDA;
+  if (e != cudaSuccess) {  // nothing launched; leave no error pending
+    cudaGetLastError();
+    return SLDG_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) return SLDG_ERR_CUDA;
   k_rho_rows_noalloc<<<(unsigned)((Dx + kThreads - 1) / kThreads), kThreads, 0, st>>>(
       scratch, (int)chunks, Dx, rho_dev);
   if (cudaGetLastError() != cudaSuccess) return SLDG_ERR_CUDA;

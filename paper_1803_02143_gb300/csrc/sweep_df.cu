@@ -47,14 +47,14 @@ cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
-                                cudaStream_t st) {
+                                cudaStream_t st, int* shape) {
   double* d = static_cast<double*>(f);
   auto go = [&](auto nt) -> cudaError_t {
     constexpr int N = decltype(nt)::value;
-    if (in_df && out_df) return launch_x12_df_N<N, true, true>(d, g, ab1, s1, ab2, s2, st);
-    if (in_df) return launch_x12_df_N<N, true, false>(d, g, ab1, s1, ab2, s2, st);
-    if (out_df) return launch_x12_df_N<N, false, true>(d, g, ab1, s1, ab2, s2, st);
-    return launch_x12_df_N<N, false, false>(d, g, ab1, s1, ab2, s2, st);
+    if (in_df && out_df) return launch_x12_df_N<N, true, true>(d, g, ab1, s1, ab2, s2, st, shape);
+    if (in_df) return launch_x12_df_N<N, true, false>(d, g, ab1, s1, ab2, s2, st, shape);
+    if (out_df) return launch_x12_df_N<N, false, true>(d, g, ab1, s1, ab2, s2, st, shape);
+    return launch_x12_df_N<N, false, false>(d, g, ab1, s1, ab2, s2, st, shape);
   };
   switch (g.n) {
     case 1: return go(std::integral_constant<int, 1>());

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
 // layout does not fit (the caller then runs the two sweeps).
 template <int N, int CPL>
 cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
-                         const int* s2, cudaStream_t st) {
+                         const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
   const long long planes = g.D[2] * g.D[3];
@@ -223,16 +223,20 @@ cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (shape) {
+    shape[0] = cs;
+    shape[1] = x12_lanes_per_pair(nc0, CPL);
+  }
   return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
                             static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2);
 }
 
 template <int N>
 cudaError_t launch_x12_N(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
-                         const int* s2, cudaStream_t st) {
+                         const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0];
-  if (nc0 <= 64) return launch_x12_T<N, 2>(f, g, ab1, s1, ab2, s2, st);
-  if (nc0 <= 128) return launch_x12_T<N, 4>(f, g, ab1, s1, ab2, s2, st);
+  if (nc0 <= 64) return launch_x12_T<N, 2>(f, g, ab1, s1, ab2, s2, st, shape);
+  if (nc0 <= 128) return launch_x12_T<N, 4>(f, g, ab1, s1, ab2, s2, st, shape);
   return cudaErrorNotSupported;
 }
 

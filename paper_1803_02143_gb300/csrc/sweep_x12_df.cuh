@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
 
 template <int N, int CPL, bool IN_DF, bool OUT_DF>
 cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int* s1,
-                            const void* ab2, const int* s2, cudaStream_t st) {
+                            const void* ab2, const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N;
   const long long planes = g.D[2] * g.D[3];
@@ -197,6 +197,10 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (shape) {
+    shape[0] = cs;
+    shape[1] = x12_lanes_per_pair(nc0, CPL);
+  }
   return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
                             static_cast<const float2*>(ab1), s1, static_cast<const float2*>(ab2),
                             s2);
@@ -204,8 +208,9 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
 
 template <int N, bool IN_DF, bool OUT_DF>
 cudaError_t launch_x12_df_N(double* f, const Grid& g, const void* ab1, const int* s1,
-                            const void* ab2, const int* s2, cudaStream_t st) {
-  if (g.nc[0] <= 64) return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, g, ab1, s1, ab2, s2, st);
+                            const void* ab2, const int* s2, cudaStream_t st, int* shape) {
+  if (g.nc[0] <= 64)
+    return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, g, ab1, s1, ab2, s2, st, shape);
   return cudaErrorNotSupported;
 }
 

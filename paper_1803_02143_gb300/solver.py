@@ -74,6 +74,8 @@ class Sldg:
     layout ``Config.shape``; all work runs on ``stream`` (default: the
     current torch stream)."""
 
+    _recordings = 0  # recordings made by any context (identifiers)
+
     def __init__(self, cfg: Config, f: torch.Tensor | None = None, stream=None):
         N.load()
         self.cfg = cfg
@@ -84,6 +86,7 @@ class Sldg:
         self.f = f
         self.stream = stream if stream is not None else torch.cuda.current_stream(f.device)
         self._ctx = N.sldg_init(cfg.c(), f.data_ptr(), self.stream.cuda_stream)
+        self.recording = 0  # increments with every record(); 0: none yet
 
     # ---- life cycle -------------------------------------------------------
     def close(self):
@@ -144,6 +147,10 @@ class Sldg:
     def sweep(self, dim: int, frac: float):
         N.sldg_sweep(self._ctx, dim, frac)
 
+    def drift(self, frac: float):
+        """X1 then X2 by frac * dt: the drift kernels of a Strang step."""
+        N.sldg_drift(self._ctx, frac)
+
     def compute_fields(self):
         N.sldg_compute_fields(self._ctx)
 
@@ -175,9 +182,21 @@ class Sldg:
                              None if Ebar is None else Ebar.data_ptr())
 
     def record(self, nsteps: int, ckpt_every: int):
+        """Record nsteps Strang steps for backward(); returns W of each step.
+        ``recording`` identifies this recording (it replaces any earlier one)."""
+        self.recording = 0
         W = np.zeros(nsteps)
         N.sldg_record(self._ctx, nsteps, ckpt_every, W)
+        Sldg._recordings += 1
+        self.recording = Sldg._recordings
+        self.record_steps = nsteps
         return W
+
+    def objective(self, cW=None) -> float:
+        """J = sum_m cW[m] W_m of the last recording (cW = dt: the
+        time-integrated electric energy), computed by the library."""
+        c = None if cW is None else np.ascontiguousarray(cW, dtype=np.float64)
+        return N.sldg_objective(self._ctx, c)
 
     def backward(self, cW=None, grad: torch.Tensor | None = None):
         if grad is None:
@@ -200,6 +219,11 @@ class Sldg:
     @property
     def launch_count(self) -> int:
         return N.sldg_launch_count(self._ctx)
+
+    @property
+    def x_pass_shape(self):
+        """(CTAs per x-plane, lanes per x1 line pair) of the last fused x pass."""
+        return N.sldg_x_pass_shape(self._ctx)
 
     def timing(self, enable: bool):
         N.sldg_timing(self._ctx, enable)

@@ -50,7 +50,7 @@ def test_strerror_names_every_code(lib):
         s = N.sldg_strerror(code)
         assert s and s != "unknown status"
     assert N.sldg_strerror(-99) == "unknown status"
-    assert N.sldg_abi_version() == 1
+    assert N.sldg_abi_version() == 2
 
 
 def _cfg(**kw):
@@ -89,6 +89,25 @@ def test_init_rejects_bad_pointers_on_host(lib):
     c.flags = 32  # unknown flag bit
     assert lib.sldg_init(ctypes.byref(c), ctypes.c_void_p(16), None,
                          ctypes.byref(out)) == N.SLDG_ERR_BAD_CONFIG
+
+
+@pytest.mark.parametrize("bad", [dict(lo=(0, 0, float("-inf"), -6)), dict(hi=(12.56, 12.56, float("inf"), 6)),
+                                 dict(hi=(12.56, float("nan"), 6, 6)), dict(degree=4),
+                                 dict(precision="fp16")])
+def test_rho_noalloc_rejects_what_init_rejects(lib, bad):
+    # the allocation-free charge density validates its configuration like
+    # sldg_init, on the host, before any CUDA call
+    from paper_1803_02143_gb300 import _native as N
+
+    c = _cfg(**bad)
+    if bad.get("precision") == "fp16":
+        c.precision = 7
+    assert lib.sldg_rho_noalloc(ctypes.byref(c), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                None) == N.SLDG_ERR_BAD_CONFIG
+    c = _cfg()
+    c.flags = 64  # unknown flag bit
+    assert lib.sldg_rho_noalloc(ctypes.byref(c), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                None) == N.SLDG_ERR_BAD_CONFIG
 
 
 def test_null_context_is_rejected(lib):

@@ -11,6 +11,8 @@
   slots that remain after the checkpoint pool; the FP32 electric-energy
   history is within 1e-5 of the FP64 one and the FP32 gradient dJ/d(alpha)
   within 1e-4 of the FP64 central difference.
+- An allocation the device cannot hold (a checkpoint pool larger than all of
+  HBM) fails with SLDG_ERR_OOM and leaves the context usable; nothing faults.
 """
 import numpy as np
 import pytest
@@ -154,3 +156,33 @@ def test_mixed_workload_forward_adjoint_fits_and_matches_fp64(lib):
     assert np.abs(W32 - W64).max() < 1e-5 * np.abs(W64).max()
     assert abs(J32 - J64) < 1e-5 * abs(J64)
     assert abs(ga - fd) < 1e-4 * abs(fd), (ga, fd)
+
+
+def test_checkpoint_pool_beyond_hbm_is_oom_and_context_survives(lib, orc):
+    from inputs import LANDAU_HI, LANDAU_LO
+
+    # 64^2 x 128^2 nodal values of degree 1: 0.54 GB per copy of f
+    cfg = lib.Config(degree=1, ncell=(32, 32, 64, 64), lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1)
+    fb = cfg.numel * 8
+    total = torch.cuda.get_device_properties(0).total_memory
+    nsteps = total // fb + 8  # one checkpoint per step: a pool larger than the device
+    params = (0.5, 0.5, 0.5)
+    s = lib.Sldg(cfg)
+    s.set_initial(0, params)
+    f0 = s.f.clone()
+    with pytest.raises(lib.SldgError) as e:
+        s.record(int(nsteps), 1)
+    assert e.value.code == lib._native.SLDG_ERR_OOM
+    torch.cuda.synchronize()  # no CUDA error is pending or sticky
+    assert torch.equal(s.f, f0)  # nothing ran
+    # the context still steps, records and differentiates like a fresh one
+    s.step(2)
+    with lib.Sldg(cfg) as t:
+        t.set_initial(0, params)
+        t.step(2)
+        assert torch.equal(s.f, t.f)
+    s.set_initial(0, params)
+    W = s.record(3, 2)
+    J, grad = s.backward()
+    assert np.isfinite(W).all() and np.isfinite(J) and torch.isfinite(grad).all()
+    s.close()

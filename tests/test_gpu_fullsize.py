@@ -1,16 +1,23 @@
-"""Parity at full size, in the launch configuration bench.py times: the
-bench workload (nonlinear Landau damping, 64^4 cells, degree 2, 1.36e9 nodal
-values), the two-stream workload (64^2 x 128^2 cells, degree 2, 5.4e9 values)
-the large mixed-precision workload (128^4 cells, degree 1, 4.3e9 values,
-FP32 storage), the paper's dG4 Landau run (36^4 cells, degree 3, 4.3e8
-values) and the cubic-spline comparison method at 128^4 points.
+"""Parity at full size: the nonlinear Landau workload (64^4 cells, degree 2,
+1.36e9 nodal values), the two-stream workload (64^2 x 128^2 cells, degree 2,
+5.4e9 values), the large mixed-precision workload (128^4 cells, degree 1,
+4.3e9 values, FP32 storage), the paper's dG4 Landau run (36^4 cells, degree
+3, 4.3e8 values) and the cubic-spline comparison method at 128^4 points.
 
-The oracle cannot step 1.36e9 values, so each stage of the Strang step is
-run alone through the C ABI (the same kernels sldg_step launches) and
-sampled outputs are recomputed one by one by the oracle: whole lines for the
-sweeps (the oracle's 1D advection of the gathered input line with the
-line's own shift), single x-nodes for rho (the oracle's v-quadrature of the
-gathered v-plane), and the full Poisson map of the GPU's rho.
+The oracle cannot step billions of values, so each stage of the Strang step
+is run alone through the C ABI and sampled outputs are recomputed one by one
+by the oracle:
+  - the x drifts through sldg_drift, which launches the kernels a Strang
+    step launches for them (the fused X1 X2 pass over each x-plane, in the
+    cluster shape of the step, asserted): whole sampled x-planes against
+    the oracle's X1 then X2 on the gathered plane;
+  - single sweeps through sldg_sweep: the v-sweeps are the kernels of the
+    step's kicks; the x-sweeps run the separate x1 and x2 kernels (used by
+    the step only where the fused pass does not apply, e.g. degree 3 in
+    FP64 or SLDG_FLAG_NO_XFUSION): whole sampled lines against the
+    oracle's 1D advection of the gathered input line with its own shift;
+  - rho at single x-nodes (the oracle's v-quadrature of the gathered
+    v-plane) and the full Poisson map of the GPU's rho.
 """
 import numpy as np
 import pytest
@@ -130,3 +137,37 @@ def test_fullsize_rho_and_poisson(big, orc, name, prec):
     R1, R2 = orc.poisson(og, rho)
     scale = max(np.abs(R1).max(), np.abs(R2).max())
     assert np.abs(E1 - R1).max() < 1e-12 * scale and np.abs(E2 - R2).max() < 1e-12 * scale
+
+
+DRIFT_CASES = [("nonlinear_landau_64", "fp64"), ("nonlinear_landau_64", "fp32"),
+               ("two_stream_64x128", "fp64"), ("two_stream_64x128", "fp32")]
+NPLANES = 6
+
+
+@pytest.mark.parametrize("name,prec", DRIFT_CASES)
+def test_fullsize_fused_drift_sampled_planes(big, orc, name, prec):
+    s, og = _context(big, orc, name, prec)
+    F = s.f
+    r = rng(2024)
+    i3 = r.integers(0, og.D(3), NPLANES)
+    i2 = r.integers(0, og.D(2), NPLANES)
+    it3, it2 = torch.from_numpy(i3).cuda(), torch.from_numpy(i2).cuda()
+    before = F[it3, it2].double().cpu().numpy()  # (planes, D_x2, D_x1)
+    s.timing(True)
+    s.drift(0.5)
+    t = s.timing_read()
+    s.timing(False)
+    assert t["x12"][1] == 1 and t["x1"][1] == 0 and t["x2"][1] == 0
+    assert s.x_pass_shape == ((4 if prec == "fp64" else 2), 32)
+    after = F[it3, it2].double().cpu().numpy()
+    h0, h1 = og.h(0), og.h(1)
+    worst = 0.0
+    for k in range(NPLANES):
+        a1 = og.nodes(2)[i2[k]] * og.dt * 0.5
+        a2 = og.nodes(3)[i3[k]] * og.dt * 0.5
+        P = before[k]
+        X1 = np.stack([orc.advect_line(og.deg, og.nc[0], h0, a1, True, P[j]) for j in range(og.D(1))])
+        X2 = np.stack([orc.advect_line(og.deg, og.nc[1], h1, a2, True, X1[:, i])
+                       for i in range(og.D(0))], axis=1)
+        worst = max(worst, np.abs(after[k] - X2).max() / max(np.abs(X2).max(), 1e-300))
+    assert worst < (2e-13 if prec == "fp64" else 4e-6), worst

@@ -360,3 +360,94 @@ def test_step_graph_replay_matches_eager_steps(lib, orc, prec):
         res.append((get(s), W))
         s.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+# The fused X1 X2 pass in the launch shape of the full-size workloads: 64
+# x1-cells of degree 2 (192-value lines) give whole warps per line pair in
+# the X1 phase; 64 x2-cells split an FP64 x-plane over a cluster of 4 CTAs
+# (FP32: 2).  (40, 64): a line length that is not a power of two, same
+# cluster sizes.  Full Strang steps against the oracle's steps.
+BENCH_X_GRIDS = [(2, (64, 64, 3, 2)), (2, (40, 64, 4, 3))]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("deg,nc", BENCH_X_GRIDS)
+def test_bench_x_pass_shape_strang_steps(lib, orc, deg, nc, prec):
+    params = (0.5, 0.5, 0.5)
+    s, og = make(lib, orc, deg, nc, dt=0.05, prec=prec)
+    s.set_initial(0, params)
+    s.timing(True)  # eager launches, counted per kernel class
+    W = s.step(2, history=True)
+    t = s.timing_read()
+    s.timing(False)
+    assert t["x12"][1] == 4 and t["x1"][1] == 0 and t["x2"][1] == 0  # two fused passes per step
+    assert s.x_pass_shape == ((4 if prec == "fp64" else 2), 32)
+    ref, Wr, _, _ = orc.step(og, orc.init(og, 0, params), 2)
+    tol = 2 * TOL64_STEP if prec == "fp64" else 1e-5
+    assert relerr(get(s), ref.reshape(og.shape)) < tol
+    assert relerr(W, Wr) < (1e-11 if prec == "fp64" else 1e-5)
+    # one more step replayed as a CUDA graph (the path of sldg_step(n >= 2))
+    W2 = s.step(2, history=True)
+    ref2, Wr2, _, _ = orc.step(og, ref, 2)
+    assert relerr(get(s), ref2.reshape(og.shape)) < 2 * tol
+    assert relerr(W2, Wr2) < (1e-11 if prec == "fp64" else 1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_drift_entry_point_is_the_step_drift(lib, orc, prec):
+    # sldg_drift runs X1 X2 with the kernels of the step's drifts: the
+    # oracle's two sweeps on random data, and the fused pass was used
+    deg, nc = BENCH_X_GRIDS[1]
+    s, og = make(lib, orc, deg, nc, dt=0.05, prec=prec)
+    f = random_f(og.shape, seed=21)
+    if prec == "fp32":
+        f = f.astype(np.float32).astype(np.float64)
+    put(s, f)
+    s.timing(True)
+    s.drift(0.5)
+    t = s.timing_read()
+    s.timing(False)
+    assert t["x12"][1] == 1
+    ref = orc.sweep(og, 1, orc.sweep(og, 0, f, frac=0.5), frac=0.5).reshape(og.shape)
+    assert relerr(get(s), ref) < (2 * TOL64 if prec == "fp64" else 2 * TOL32)
+    s.close()
+
+
+def test_objective_and_weight_count(lib, orc):
+    # J of a recording from the library (no arithmetic in Python), the
+    # weight count checked against the recorded steps
+    s, og = make(lib, orc, 1, (6, 5, 8, 7), dt=0.1)
+    s.set_initial(0, (0.5, 0.5, 0.5))
+    W = s.record(5, 2)
+    c = np.linspace(0.1, 0.5, 5)
+    J = s.objective(c)
+    Jr, _, Wr = orc.backward(og, orc.init(og, 0, (0.5, 0.5, 0.5)), 5, 2, cW=c)
+    assert abs(J - Jr) < 1e-12 * abs(Jr)
+    assert abs(s.objective() - 0.1 * np.sum(W)) < 1e-13 * abs(s.objective())
+    with pytest.raises(lib.SldgError) as e:
+        s.objective(c[:4])
+    assert e.value.code == lib._native.SLDG_ERR_ARG
+    with pytest.raises(lib.SldgError) as e:
+        s.backward(np.ones(7))
+    assert e.value.code == lib._native.SLDG_ERR_ARG
+    J2, _ = s.backward(c)
+    assert J2 == J
+    s.close()
+
+
+def test_autograd_refuses_a_stale_recording(lib, orc):
+    from paper_1803_02143_gb300.autograd import time_integrated_energy
+
+    s, og = make(lib, orc, 1, (6, 5, 8, 7), dt=0.1)
+    f0 = torch.from_numpy(orc.init(og, 0, (0.5, 0.5, 0.5)).reshape(og.shape)).cuda()
+    a = f0.clone().requires_grad_(True)
+    b = (1.01 * f0).requires_grad_(True)
+    Ja = time_integrated_energy(a, s, 3, 2)
+    Jb = time_integrated_energy(b, s, 4, 2)  # the solver now holds b's recording
+    with pytest.raises(RuntimeError):
+        Ja.backward()
+    Jb.backward()
+    _, gr, _ = orc.backward(og, b.detach().cpu().numpy(), 4, 2)
+    assert relerr(b.grad.cpu().numpy(), gr.reshape(og.shape)) < 1e-11
+    s.close()

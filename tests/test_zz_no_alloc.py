@@ -36,6 +36,13 @@ def test_rho_without_allocation_matches_context_rho(P, prec):
     cases = [
         (2, (12, 10, 9, 11), LANDAU_LO, LANDAU_HI, 31),  # first call on the device
         (1, (7, 9, 14, 6), TSI_LO, TSI_HI, 32),          # second call, other grid and data
+        # a large x-plane over few v-cells: the scratch limits the chunks to
+        # 3 of 342 v-planes each (weights filled by a strided loop)
+        (3, (100, 100, 8, 8), LANDAU_LO, LANDAU_HI, 33),
+        # many v-planes: the chunk count is capped at 32
+        (1, (4, 4, 64, 64), TSI_LO, TSI_HI, 34),
+        # an x-plane just below the scratch size: a single chunk
+        (1, (362, 362, 2, 2), LANDAU_LO, LANDAU_HI, 35),
     ]
     stream = torch.cuda.current_stream()
     for deg, nc, lo, hi, seed in cases:
