@@ -229,7 +229,8 @@ KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df.cu"), ("k_sweep_strided_df3", "swee
 
 def _kernel_kind(name):
     """(kind, precision) of a sweep kernel from its ncu name, or None."""
-    prec = "fp64" if ("_df" in name or "double" in name) else "fp32"
+    base = name.split("(")[0]  # template arguments only, not the parameter list
+    prec = "fp64" if ("_df" in base or "double" in base) else "fp32"
     if "k_sweep_x12" in name:
         return "x12", prec
     if "k_sweep_x1" in name:
@@ -258,12 +259,17 @@ def ingest_ncu(args):
 
     from paper_1803_02143_gb300 import configs
 
-    out = subprocess.run(["ncu", "-i", args.ingest_ncu, "--page", "raw", "--csv", "--metrics",
-                          NCU_METRICS], capture_output=True, text=True, check=True).stdout
+    out = subprocess.run(["ncu", "-i", args.ingest_ncu, "--page", "raw", "--csv",
+                          "--print-units", "base", "--metrics", NCU_METRICS],
+                         capture_output=True, text=True, check=True).stdout
     rows = list(csv.reader(io.StringIO(out)))
-    head = rows[0]
+    head, units = rows[0], rows[1]
     data = [r for r in rows[2:] if len(r) == len(head)]
     col = {h: i for i, h in enumerate(head)}
+    # values to bytes and nanoseconds whatever scale the report prints
+    scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+             "ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6,
+             "s": 1e9, "second": 1e9}
     case = configs.workload(args.ncu_case)
     by_kind, table = {}, []
     vcount = {}
@@ -272,9 +278,11 @@ def ingest_ncu(args):
         kk = _kernel_kind(name)
 
         def num(metric):
-            v = r[col[metric]].replace(",", "") if metric in col else ""
+            if metric not in col:
+                return float("nan")
+            v = r[col[metric]].replace(",", "")
             try:
-                return float(v)
+                return float(v) * scale.get(units[col[metric]].strip().lower(), 1.0)
             except ValueError:
                 return float("nan")
 

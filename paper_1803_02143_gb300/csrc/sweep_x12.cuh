@@ -31,6 +31,13 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" :::
                    "memory");
 }
+// the two halves of cluster_sync, for work between signalling and waiting
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 // shared-memory address of the same variable in CTA `rank` of the cluster
 __device__ __forceinline__ unsigned cluster_map(const void* p, unsigned rank) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);

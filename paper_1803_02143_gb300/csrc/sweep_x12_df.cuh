@@ -3,6 +3,8 @@
 // sweep_df3.cuh).
 #pragma once
 
+#include <algorithm>
+
 #include "sweep_df3.cuh"
 #include "sweep_x12.cuh"
 
@@ -15,7 +17,16 @@ namespace sldg {
 // the operand layout of X2 (lanes = two adjacent columns); X2 writes 8-byte
 // elements to f (pairs when OUT_DF).  Matrices: (hi, hi, lo, lo) float4 per
 // entry in shared memory.
+//
+// The cluster barrier between X1 and X2 is split: a CTA signals that its X1
+// rows are final, computes the X2 outputs whose source cells all lie in its
+// own rows, and only then waits for its peers before the outputs that read
+// a peer's rows.  Small CTAs (128 threads, a plane over 8 of them at 192^2
+// FP64 values: 37 KB each, six per SM) keep the phases of many CTAs
+// interleaved on each SM.  The arithmetic of every output is unchanged.
 // ---------------------------------------------------------------------------
+constexpr int kX12DfThreads = 128;
+constexpr int kX12DfSmemTarget = 38 * 1024;  // six CTAs per SM
 __device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
   float4 v;
   asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
@@ -24,9 +35,10 @@ __device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
   return v;
 }
 
+// run: consecutive x2 cells of one X2 work item (one column pair)
 template <int N, int CPL, bool GRP, bool IN_DF, bool OUT_DF>
-__global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
-    k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
+__global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
+    k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int run, int D2, int D3,
                    const float2* __restrict__ ab1, const int* __restrict__ s1,
                    const float2* __restrict__ ab2, const int* __restrict__ s2) {
   constexpr int MN = 2 * N * N;
@@ -107,25 +119,33 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
       __syncwarp(gmask);
     }
   }
-  cluster_sync();
+  __syncthreads();  // this CTA's X1 rows are final for all of its warps
+  cluster_arrive();
 
-  // X2 for the CTA's rows from column-pair operands
+  // X2 for the CTA's rows from column-pair operands: first the runs whose
+  // source cells all lie in this CTA's rows, then (after the peers' X1) the
+  // runs that read a peer's rows through distributed shared memory
   {
-    const int sa = wrap_cell(-s2[key2] - 1, nc1);
+    const int d = -s2[key2] - 1;  // sources of output cell c: c + d, c + d + 1
+    const int sa = wrap_cell(d, nc1);
     const int npairs = D0 / 2;
-    const int items = npairs * kX12Groups;
-    auto load = [&](int kcell, int c0, float2* xh, float2* xl) {
-      const int owner = kcell / cells_per;
-      const int lrow = (kcell - owner * cells_per) * N;
-      if (owner == (int)rank) {
+    const int items = npairs * ((cells_per + run - 1) / run);
+    // exact quotients of small operands (< 2^16) by a 32-bit reciprocal
+    const unsigned inv_np = 0xFFFFFFFFu / (unsigned)npairs + 1u;
+    const unsigned inv_cp = 0xFFFFFFFFu / (unsigned)cells_per + 1u;
+    auto local_load = [&](int lcell, int c0, float2* xh, float2* xl) {
 #pragma unroll
-        for (int l = 0; l < N; ++l) {
-          const float4 u = *reinterpret_cast<const float4*>(rows + (lrow + l) * D0 + c0);
-          xh[l] = make_float2(u.x, u.y);
-          xl[l] = make_float2(u.z, u.w);
-        }
+      for (int l = 0; l < N; ++l) {
+        const float4 u = *reinterpret_cast<const float4*>(rows + (lcell * N + l) * D0 + c0);
+        xh[l] = make_float2(u.x, u.y);
+        xl[l] = make_float2(u.z, u.w);
+      }
+    };
+    auto any_load = [&](int owner, int lcell, int c0, float2* xh, float2* xl) {
+      if (owner == (int)rank) {
+        local_load(lcell, c0, xh, xl);
       } else {
-        const unsigned base = cluster_map(rows + lrow * D0 + c0, (unsigned)owner);
+        const unsigned base = cluster_map(rows + lcell * N * D0 + c0, (unsigned)owner);
 #pragma unroll
         for (int l = 0; l < N; ++l) {
           const float4 u = ld_cluster_f4(base + (unsigned)(l * D0 * 8));
@@ -134,31 +154,55 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 ? 2 : 3)
         }
       }
     };
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int q = it % npairs, g = it / npairs;
-      const int c0 = 2 * q;
-      const int lb = (g * cells_per) / kX12Groups, le = ((g + 1) * cells_per) / kX12Groups;
-      if (lb >= le) continue;
-      const int cglob = (int)rank * cells_per + lb;
-      int k = cglob + sa;
-      if (k >= nc1) k -= nc1;
-      float2 ah[N], al[N], bh[N], bl[N];
-      load(k, c0, ah, al);
-      double* out = fp + (long long)(cglob * N) * D0 + c0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) cluster_wait();  // every peer's X1 rows are final
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int g = (int)__umulhi((unsigned)it, inv_np);
+        const int c0 = 2 * (it - g * npairs);
+        const int lb = g * run, le = min(lb + run, cells_per);
+        const bool local = lb + d >= 0 && le + d <= cells_per - 1;
+        if (local != (pass == 0)) continue;
+        const int cglob = (int)rank * cells_per + lb;
+        float2 ah[N], al[N], bh[N], bl[N];
+        double* out = fp + (long long)(cglob * N) * D0 + c0;
+        if (local) {
+          int k = lb + d;
+          local_load(k, c0, ah, al);
 #pragma unroll 1
-      for (int c = lb; c < le; ++c, out += N * D0) {
-        k = k + 1 == nc1 ? 0 : k + 1;
-        load(k, c0, bh, bl);
-        df3_cell<N, OUT_DF>(m2, ah, al, bh, bl, out, D0);
+          for (int c = lb; c < le; ++c, out += N * D0) {
+            local_load(++k, c0, bh, bl);
+            df3_cell<N, OUT_DF>(m2, ah, al, bh, bl, out, D0);
 #pragma unroll
-        for (int l = 0; l < N; ++l) {
-          ah[l] = bh[l];
-          al[l] = bl[l];
+            for (int l = 0; l < N; ++l) {
+              ah[l] = bh[l];
+              al[l] = bl[l];
+            }
+          }
+        } else {
+          int k = cglob + sa;
+          if (k >= nc1) k -= nc1;
+          int owner = (int)__umulhi((unsigned)k, inv_cp);
+          int lk = k - owner * cells_per;
+          any_load(owner, lk, c0, ah, al);
+#pragma unroll 1
+          for (int c = lb; c < le; ++c, out += N * D0) {
+            if (++lk == cells_per) {
+              lk = 0;
+              owner = owner + 1 == cs ? 0 : owner + 1;
+            }
+            any_load(owner, lk, c0, bh, bl);
+            df3_cell<N, OUT_DF>(m2, ah, al, bh, bl, out, D0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) {
+              ah[l] = bh[l];
+              al[l] = bl[l];
+            }
+          }
         }
       }
     }
   }
-  cluster_sync();
+  cluster_sync();  // no CTA leaves while a peer may still read its rows
 }
 
 template <int N, int CPL, bool IN_DF, bool OUT_DF>
@@ -169,25 +213,31 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 2 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
   const size_t mats = 2 * (size_t)(2 * N * N) * sizeof(float4);
+  // the smallest cluster (2 to 8 CTAs) whose row share fits six CTAs per SM,
+  // else the largest that fits one
   int cs = 0;
   for (int c = 2; c <= 8; c *= 2) {
     if (nc1 % c) continue;
     const long long H = (long long)(nc1 / c) * N;
     if (H % 2) continue;
-    if (mats + H * D0 * (long long)sizeof(double) <= 75 * 1024) {
+    const long long smem = (long long)mats + H * D0 * (long long)sizeof(double);
+    if (smem <= kX12DfSmemTarget) {
       cs = c;
       break;
     }
+    if (smem <= 227 * 1024) cs = c;
   }
   if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
-  const size_t smem = mats + (size_t)(nc1 / cs) * N * D0 * sizeof(double);
+  const int cells_per = nc1 / cs;
+  const int run = std::min(2, cells_per);  // two-cell X2 work items
+  const size_t smem = mats + (size_t)cells_per * N * D0 * sizeof(double);
   auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_df<N, CPL, true, IN_DF, OUT_DF>
                                                : k_sweep_x12_df<N, CPL, false, IN_DF, OUT_DF>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(planes * cs));
-  cfg.blockDim = dim3(kX12Threads);
+  cfg.blockDim = dim3(kX12DfThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -201,7 +251,7 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
     shape[0] = cs;
     shape[1] = x12_lanes_per_pair(nc0, CPL);
   }
-  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
+  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
                             static_cast<const float2*>(ab1), s1, static_cast<const float2*>(ab2),
                             s2);
 }

@@ -158,7 +158,7 @@ def test_fullsize_fused_drift_sampled_planes(big, orc, name, prec):
     t = s.timing_read()
     s.timing(False)
     assert t["x12"][1] == 1 and t["x1"][1] == 0 and t["x2"][1] == 0
-    assert s.x_pass_shape == ((4 if prec == "fp64" else 2), 32)
+    assert s.x_pass_shape == ((8 if prec == "fp64" else 2), 32)
     after = F[it3, it2].double().cpu().numpy()
     h0, h1 = og.h(0), og.h(1)
     worst = 0.0

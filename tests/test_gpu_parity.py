@@ -364,7 +364,7 @@ def test_step_graph_replay_matches_eager_steps(lib, orc, prec):
 
 # The fused X1 X2 pass in the launch shape of the full-size workloads: 64
 # x1-cells of degree 2 (192-value lines) give whole warps per line pair in
-# the X1 phase; 64 x2-cells split an FP64 x-plane over a cluster of 4 CTAs
+# the X1 phase; 64 x2-cells split an FP64 x-plane over a cluster of 8 CTAs
 # (FP32: 2).  (40, 64): a line length that is not a power of two, same
 # cluster sizes.  Full Strang steps against the oracle's steps.
 BENCH_X_GRIDS = [(2, (64, 64, 3, 2)), (2, (40, 64, 4, 3))]
@@ -381,7 +381,7 @@ def test_bench_x_pass_shape_strang_steps(lib, orc, deg, nc, prec):
     t = s.timing_read()
     s.timing(False)
     assert t["x12"][1] == 4 and t["x1"][1] == 0 and t["x2"][1] == 0  # two fused passes per step
-    assert s.x_pass_shape == ((4 if prec == "fp64" else 2), 32)
+    assert s.x_pass_shape == ((8 if prec == "fp64" else 2), 32)
     ref, Wr, _, _ = orc.step(og, orc.init(og, 0, params), 2)
     tol = 2 * TOL64_STEP if prec == "fp64" else 1e-5
     assert relerr(get(s), ref.reshape(og.shape)) < tol
@@ -450,4 +450,24 @@ def test_autograd_refuses_a_stale_recording(lib, orc):
     Jb.backward()
     _, gr, _ = orc.backward(og, b.detach().cpu().numpy(), 4, 2)
     assert relerr(b.grad.cpu().numpy(), gr.reshape(og.shape)) < 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("deg,nc,dt", [(2, (40, 64, 3, 2), 1.0), (1, (16, 24, 4, 3), 2.0)])
+def test_fused_drift_shifts_of_many_cells(lib, orc, deg, nc, dt, prec):
+    # x-shifts of up to 15 cells: most X2 outputs read rows held by CTAs
+    # several places away in the cluster (wrapping around the plane)
+    s, og = make(lib, orc, deg, nc, dt=dt, prec=prec)
+    f = random_f(og.shape, seed=23)
+    if prec == "fp32":
+        f = f.astype(np.float32).astype(np.float64)
+    put(s, f)
+    s.timing(True)
+    s.drift(0.5)
+    t = s.timing_read()
+    s.timing(False)
+    assert t["x12"][1] == 1 and s.x_pass_shape[0] >= (2 if prec == "fp64" else 1)
+    ref = orc.sweep(og, 1, orc.sweep(og, 0, f, frac=0.5), frac=0.5).reshape(og.shape)
+    assert relerr(get(s), ref) < (2 * TOL64 if prec == "fp64" else 2 * TOL32)
     s.close()
