@@ -309,13 +309,19 @@ void invalidate_vmats(sldg_ctx* c) { c->vm[0].valid = c->vm[1].valid = false; }
 
 // ---- sweeps ---------------------------------------------------------------------------
 // in_df / out_df: FP64 double-float sweeps read / write (hi, lo) pairs
+// out (nullable): outputs to out and buf left unchanged (kernels that write
+// in place only run on out after a copy).  g_df: gfwd holds double-float
+// pairs (FP64 contexts) instead of IEEE doubles.
 int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const void* gfwd,
-              double* Ebar, bool in_df = false, bool out_df = false) {
+              double* Ebar, bool in_df = false, bool out_df = false, void* out = nullptr,
+              bool g_df = false) {
   const Grid& g = c->g;
   if (spline(c) && adjoint) return SLDG_ERR_UNSUPPORTED;
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.f = buf;
+  a.out = out;
+  a.g_df = g_df ? 1 : 0;
   a.prec = c->prec;
   a.n = g.n;
   a.dim = dim;
@@ -380,29 +386,51 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
     a.epart = c->d_epart;
   }
   const int kind = adjoint ? (dim < 2 ? SLDG_K_ADJ_X : SLDG_K_ADJ_V) : SLDG_K_X1 + dim;
+  bool swept = false;  // the transposed sweep ran with the partials
   if (ebar_df) {  // partials of d/dE <lam, S g> from the adjoint before the sweep
     KTimer t(c, kind);
     SweepArgs ae = a;
     ae.s = m->s;  // the forward shifts (a carries the transposed form)
-    const cudaError_t e = launch_ebar_df(ae, c->stream);
+    ae.tab2 = m->abt2;  // and the transposed sweep from the same staged tile
+    ae.ts = m->st;
+    cudaError_t e = out_of_place(a) ? cudaErrorNotSupported : launch_ebar_df(ae, c->stream);
+    swept = e == cudaSuccess;
+    if (e == cudaErrorNotSupported) {  // the partials alone, the sweep separately
+      ae.tab2 = nullptr;
+      ae.ts = nullptr;
+      e = launch_ebar_df(ae, c->stream);
+    }
     if (e == cudaErrorNotSupported) {  // layout not taken: the fused FP64 FMA kernel
       t.n = 0;
       a.ab = m->ab;
       a.ab2 = m->ab2;
       a.s = m->s;
       a.adjoint = 1;
+      if (a.g_df) {  // that kernel reads the forward input as IEEE doubles
+        SLDG_CU(launch_df_to_ieee(gfwd, const_cast<void*>(gfwd), g.N, c->stream));
+        c->launches += 1;
+        a.g_df = 0;
+      }
     } else if (e != cudaSuccess) {
       cudaGetLastError();
       return SLDG_ERR_CUDA;
     }
   }
-  {
+  if (!swept) {
+    auto launch = [&](const SweepArgs& x) {
+      if (spline(c)) return launch_spline_sweep(x, c->stream);
+      if (c->prec == SLDG_FP32) return launch_sweep_f32(x, c->stream);
+      if (x.adjoint || x.native_fp64) return launch_sweep_f64(x, c->stream);
+      return launch_sweep_df(x, c->stream);
+    };
     KTimer t(c, kind);
-    cudaError_t e;
-    if (spline(c)) e = launch_spline_sweep(a, c->stream);
-    else if (c->prec == SLDG_FP32) e = launch_sweep_f32(a, c->stream);
-    else if (a.adjoint || a.native_fp64) e = launch_sweep_f64(a, c->stream);
-    else e = launch_sweep_df(a, c->stream);
+    cudaError_t e = launch(a);
+    if (e == cudaErrorNotSupported && out_of_place(a)) {  // in place on a copy
+      SLDG_CU(cudaMemcpyAsync(a.out, a.f, g.N * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+      a.f = a.out;
+      a.out = nullptr;
+      e = launch(a);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       return SLDG_ERR_CUDA;
@@ -441,8 +469,9 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // trans: the transposed sweeps X1^T then X2^T (the adjoint of the pair, which
 // commute like X1 and X2), run in forward form on the transposed tables
 // ([B^T; A^T], shift entries -s - 1) like the separate adjoint x-sweeps
+// out (nullable): the result goes there and buf is left unchanged
 int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done,
-            bool trans = false) {
+            bool trans = false, void* out = nullptr) {
   *done = false;
   if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE))
     return SLDG_OK;
@@ -455,10 +484,10 @@ int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* 
   const cudaError_t e =
       c->prec == SLDG_FP32
           ? launch_sweep_x12_f32(buf, c->g, trans ? m0->abt : m0->ab, s0,
-                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape)
+                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape, out)
           : launch_sweep_x12_df(buf, c->g, trans ? m0->abt2 : m0->ab2, s0,
                                 trans ? m1->abt2 : m1->ab2, s1, in_df ? 1 : 0, out_df ? 1 : 0,
-                                c->stream, c->x12_shape);
+                                c->stream, c->x12_shape, out);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -471,14 +500,20 @@ int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* 
   return SLDG_OK;
 }
 
-// X1(frac tau) X2(frac tau): the fused pass, or the two sweeps
-int drift(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df) {
+// X1(frac tau) X2(frac tau): the fused pass, or the two sweeps; out
+// (nullable): the result goes there and buf is left unchanged
+int drift(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, void* out = nullptr) {
   const bool df = in_df || out_df;
   bool fused = false;
-  SLDG_TRY(run_x12(c, buf, frac, in_df, out_df, &fused));
+  SLDG_TRY(run_x12(c, buf, frac, in_df, out_df, &fused, false, out));
   if (!fused) {
-    SLDG_TRY(run_sweep(c, buf, 0, frac, false, nullptr, nullptr, in_df, df));
-    SLDG_TRY(run_sweep(c, buf, 1, frac, false, nullptr, nullptr, df, out_df));
+    void* w = buf;
+    if (out && out != buf) {
+      SLDG_CU(cudaMemcpyAsync(out, buf, c->g.N * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+      w = out;
+    }
+    SLDG_TRY(run_sweep(c, w, 0, frac, false, nullptr, nullptr, in_df, df));
+    SLDG_TRY(run_sweep(c, w, 1, frac, false, nullptr, nullptr, df, out_df));
   }
   return SLDG_OK;
 }
@@ -591,39 +626,31 @@ int prepare_xmats(sldg_ctx* c) {
   return SLDG_OK;
 }
 
-// Step m of the forward again from its state in buf, keeping what the
-// adjoint of the step needs: g2 (the input of V1, after the x half drifts),
-// g3 (the input of V2, after V1) as IEEE doubles, and the kick field (E_out,
-// 2 D_0 D_1 doubles, nullable; the context's field holds it as well).  buf
-// follows exactly the states of do_step (the same kernels and formats), so a
-// recomputed trajectory is the recorded one bit for bit.  g3_out may be buf
-// itself when !full (converted in place).  full: finish the step in buf.
-int forward_stage(sldg_ctx* c, void* buf, void* g2_out, void* g3_out, double* E_out, bool full) {
+// Step m of the forward again from its state src (IEEE doubles on FP64
+// storage; not modified), keeping what the adjoint of the step needs: g2
+// (the input of V1, after the x half drifts) and g3 (the input of V2, after
+// V1) in the format of the step's intermediate states (double-float pairs
+// when the sweeps run in double-float arithmetic), and the kick field
+// (E_out, 2 D_0 D_1 doubles, nullable; the context's field holds it as
+// well).  Every sweep writes out of place into the next buffer, so nothing
+// is copied, and the states are those of do_step bit for bit (the same
+// kernels, arithmetic and formats).  full: finish the step into dst (which
+// may be src; its previous contents are overwritten).
+int forward_stage(sldg_ctx* c, const void* src, void* g2_out, void* g3_out, double* E_out,
+                  bool full, void* dst) {
   const bool df = df_states(c);
-  const size_t fb = c->g.N * c->esize;
-  auto take = [&](void* dst) -> int {  // IEEE copy of the current state
-    if (df) {
-      SLDG_CU(launch_df_to_ieee(buf, dst, c->g.N, c->stream));
-      c->launches += 1;
-    } else if (dst != buf) {
-      SLDG_CU(cudaMemcpyAsync(dst, buf, fb, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    return SLDG_OK;
-  };
-  SLDG_TRY(drift(c, buf, 0.5, false, df));
-  SLDG_TRY(compute_fields(c, buf, df));
+  SLDG_TRY(drift(c, const_cast<void*>(src), 0.5, false, df, g2_out));
+  SLDG_TRY(compute_fields(c, g2_out, df));
   if (E_out) {
     SLDG_CU(cudaMemcpyAsync(E_out, c->d_E[0], c->g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
                             c->stream));
     SLDG_CU(cudaMemcpyAsync(E_out + c->g.Dx, c->d_E[1], c->g.Dx * sizeof(double),
                             cudaMemcpyDeviceToDevice, c->stream));
   }
-  SLDG_TRY(take(g2_out));
-  SLDG_TRY(run_sweep(c, buf, 2, 1.0, false, nullptr, nullptr, df, df));
-  if (!full) return take(g3_out);
-  SLDG_TRY(take(g3_out));
-  SLDG_TRY(run_sweep(c, buf, 3, 1.0, false, nullptr, nullptr, df, df));
-  return drift(c, buf, 0.5, df, false);
+  SLDG_TRY(run_sweep(c, g2_out, 2, 1.0, false, nullptr, nullptr, df, df, g3_out));
+  if (!full) return SLDG_OK;
+  SLDG_TRY(run_sweep(c, g3_out, 3, 1.0, false, nullptr, nullptr, df, df, dst));
+  return drift(c, dst, 0.5, df, false);
 }
 
 // The repeated unit of sldg_step: a whole step (IEEE in and out), or with
@@ -1227,8 +1254,9 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
   SLDG_CU(cudaMemsetAsync(c->d_Eb[0], 0, g.Dx * sizeof(double), c->stream));
   SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
   SLDG_TRY(adjoint_drift(c, grad));
-  SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1]));
-  SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0]));
+  const bool gdf = df_states(c);  // g2, g3 as forward_stage keeps them
+  SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1], false, false, nullptr, gdf));
+  SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0], false, false, nullptr, gdf));
   {
     KTimer t(c, SLDG_K_OTHER);
     SLDG_CU(launch_energy_adj(c->d_Eb[0], c->d_Eb[1], c->d_E[0], c->d_E[1], c->d_wx, g.Dx,
@@ -1249,11 +1277,9 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
 // The same from the step's initial state fm (recomputing g2, g3 and the
 // field in the two work buffers)
 int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad) {
-  const size_t fb = c->g.N * c->esize;
   void* g2 = c->d_work[0];
   void* g3 = c->d_work[1];
-  SLDG_CU(cudaMemcpyAsync(g3, fm, fb, cudaMemcpyDeviceToDevice, c->stream));
-  SLDG_TRY(forward_stage(c, g3, g2, g3, nullptr, false));
+  SLDG_TRY(forward_stage(c, fm, g2, g3, nullptr, false, nullptr));
   return adjoint_step_from(c, g2, g3, nullptr, m, cW, grad);
 }
 
@@ -1282,11 +1308,11 @@ int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>
     // one forward pass over the range keeps every step's g2, g3 and field
     std::vector<char*> st(free.end() - (2 * n + 1), free.end());
     free.resize(free.size() - (2 * n + 1));
-    char* w = st[2 * n];
-    SLDG_CU(cudaMemcpyAsync(w, src, fb, cudaMemcpyDeviceToDevice, c->stream));
+    char* w = st[2 * n];  // the running state from step a + 1 on (src is kept)
     const long long e2 = 2 * c->g.Dx;
     for (int i = 0; i < n; ++i) {
-      SLDG_TRY(forward_stage(c, w, st[2 * i], st[2 * i + 1], c->d_Ecap + i * e2, i + 1 < n));
+      SLDG_TRY(forward_stage(c, i == 0 ? src : w, st[2 * i], st[2 * i + 1], c->d_Ecap + i * e2,
+                             i + 1 < n, w));
       if (i + 1 < n) c->bwd_recomputed += 1;
     }
     for (int m = b - 1; m >= a; --m)

@@ -36,6 +36,9 @@ struct MatSet {
 // Everything a sweep launch needs.
 struct SweepArgs {
   void* f;             // in place, N elements
+  void* out;           // or null: outputs to out (N elements), f read only; only the
+                       // strided kernels take it (launch_sweep_* return
+                       // cudaErrorNotSupported for the others)
   const void* g;       // forward input for the shift derivative (adjoint v-sweeps), or null
   double* epart;       // partial sums of the shift derivative, or null
   int prec;            // SLDG_FP64 / SLDG_FP32
@@ -58,7 +61,13 @@ struct SweepArgs {
   int native_fp64;     // FP64 storage: 1 = FP64 FMA kernels, 0 = double-float kernels
   int in_df;           // double-float kernels: input elements are (hi, lo) pairs
   int out_df;          // double-float kernels: write (hi, lo) pairs instead of doubles
+  int g_df;            // g holds (hi, lo) pairs instead of doubles (FP64 contexts)
+  const void* tab2;    // shift-derivative kernel of FP64 contexts: with ts non-null it also
+  const int* ts;       // applies the transposed sweep (pairs tab2, shifts ts) in place
 };
+
+// An out-of-place request (outputs to a buffer other than the input).
+inline bool out_of_place(const SweepArgs& a) { return a.out && a.out != a.f; }
 
 // Kernel launchers (sweep_f64.cu / sweep_f32.cu).
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st);  // FP64 FMA
@@ -74,15 +83,16 @@ cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 // fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the
 // layout does not fit.  shape (nullable, two ints): the launch's CTAs per
-// x-plane (cluster size) and lanes per x1 line pair of its X1 phase.
+// x-plane (cluster size) and lanes per x1 line pair of its X1 phase.  out
+// (nullable): write the result there and leave f unchanged.
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
                                  const void* ab2, const int* s2, cudaStream_t st,
-                                 int* shape = nullptr);
+                                 int* shape = nullptr, void* out = nullptr);
 // the same for FP64 storage in double-float arithmetic (sweep_df.cu); ab1, ab2
 // are the (hi, lo) float-pair tables, in_df / out_df the element formats
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
-                                cudaStream_t st, int* shape = nullptr);
+                                cudaStream_t st, int* shape = nullptr, void* out = nullptr);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
 // SLDG_OK or SLDG_ERR_BAD_CONFIG: the configuration checks of sldg_init (api.cu)
 int validate_config(const sldg_config* cfg);

@@ -193,6 +193,7 @@ cudaError_t launch_spline_P(const SweepArgs& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_spline_sweep(const SweepArgs& a, cudaStream_t st) {
+  if (out_of_place(a)) return cudaErrorNotSupported;  // in place only
   if (a.n != 1 || !a.periodic || a.adjoint) return cudaErrorNotSupported;
   return a.prec == SLDG_FP32 ? launch_spline_P<float>(a, st) : launch_spline_P<double>(a, st);
 }

@@ -14,7 +14,7 @@ static cudaError_t launch_sweep_df_n4(const SweepArgs& a, cudaStream_t st) {
   if (a.adjoint || (reinterpret_cast<uintptr_t>(a.f) & 15)) return cudaErrorNotSupported;
   auto go = [&](auto in_t, auto out_t) -> cudaError_t {
     constexpr bool I = decltype(in_t)::value, O = decltype(out_t)::value;
-    if (a.dim == 0) return launch_x1_warp_T<4, I, O>(a, st);
+    if (a.dim == 0) return out_of_place(a) ? cudaErrorNotSupported : launch_x1_warp_T<4, I, O>(a, st);
     if (a.inner % 2) return cudaErrorNotSupported;
     return launch_strided_df3_T<4, I, O>(a, st);
   };
@@ -28,7 +28,7 @@ static cudaError_t launch_sweep_df_n4(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_sweep_df(const SweepArgs& a, cudaStream_t st) {
   const cudaError_t e = a.n == 4 ? launch_sweep_df_n4(a, st) : launch_sweep_df2(a, st);
-  if (e != cudaErrorNotSupported) return e;
+  if (e != cudaErrorNotSupported || out_of_place(a)) return e;
   if (a.in_df && a.out_df) return launch_sweep_any<PolDFT<true, true>>(a, st);
   if (a.in_df) return launch_sweep_any<PolDFT<true, false>>(a, st);
   if (a.out_df) return launch_sweep_any<PolDFT<false, true>>(a, st);
@@ -47,14 +47,15 @@ cudaError_t launch_ebar_df(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
-                                cudaStream_t st, int* shape) {
-  double* d = static_cast<double*>(f);
+                                cudaStream_t st, int* shape, void* out) {
+  const double* d = static_cast<const double*>(f);
+  double* o = static_cast<double*>(out ? out : f);
   auto go = [&](auto nt) -> cudaError_t {
     constexpr int N = decltype(nt)::value;
-    if (in_df && out_df) return launch_x12_df_N<N, true, true>(d, g, ab1, s1, ab2, s2, st, shape);
-    if (in_df) return launch_x12_df_N<N, true, false>(d, g, ab1, s1, ab2, s2, st, shape);
-    if (out_df) return launch_x12_df_N<N, false, true>(d, g, ab1, s1, ab2, s2, st, shape);
-    return launch_x12_df_N<N, false, false>(d, g, ab1, s1, ab2, s2, st, shape);
+    if (in_df && out_df) return launch_x12_df_N<N, true, true>(d, o, g, ab1, s1, ab2, s2, st, shape);
+    if (in_df) return launch_x12_df_N<N, true, false>(d, o, g, ab1, s1, ab2, s2, st, shape);
+    if (out_df) return launch_x12_df_N<N, false, true>(d, o, g, ab1, s1, ab2, s2, st, shape);
+    return launch_x12_df_N<N, false, false>(d, o, g, ab1, s1, ab2, s2, st, shape);
   };
   switch (g.n) {
     case 1: return go(std::integral_constant<int, 1>());

@@ -335,6 +335,7 @@ cudaError_t launch_sweep_df2_T(const SweepArgs& a, cudaStream_t st) {
   const long long D = (long long)a.nc * N;
   if (a.adjoint || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
   if (a.dim == 0) {
+    if (out_of_place(a)) return cudaErrorNotSupported;
     {
       cudaError_t e3 = launch_x1_warp_T<N, IN_DF, OUT_DF>(a, st);
       if (e3 != cudaErrorNotSupported) return e3;
@@ -354,7 +355,7 @@ cudaError_t launch_sweep_df2_T(const SweepArgs& a, cudaStream_t st) {
   if (a.inner % 2) return cudaErrorNotSupported;
   {
     const cudaError_t e3 = launch_strided_df3_T<N, IN_DF, OUT_DF>(a, st);
-    if (e3 != cudaErrorNotSupported) return e3;
+    if (e3 != cudaErrorNotSupported || out_of_place(a)) return e3;
   }
   const size_t smem = strided_df2_smem(D, N);
   if (smem > 227 * 1024) return cudaErrorNotSupported;

@@ -197,7 +197,7 @@ __device__ __forceinline__ void df3_run(const double* __restrict__ raw, const fl
 // CTA for 192-node lines).  Longer lines use one buffer.
 template <int N, bool PERIODIC, bool PERCOL, bool IN_DF, bool OUT_DF>
 __global__ void __launch_bounds__(kDf3Threads, 2)
-    k_sweep_strided_df3(double* __restrict__ f, int ncols, long long rstride, long long ostride,
+    k_sweep_strided_df3(const double* f, double* out, int ncols, long long rstride, long long ostride,
                         int nc, int outer, int nbuf, const float2* __restrict__ ab2,
                         const int* __restrict__ svec, long long mcount, int key_div, int key_mod) {
   static_assert(PERCOL || PERIODIC, "the per-tile matrix form serves the periodic x2 sweep");
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
   if (nbuf == 2 && o0 < o1) issue(o0, raw);
   int b = 0;
   for (int o = o0; o < o1; o += ostep, b ^= 1) {
-    double* fb = f + (long long)o * ostride + col0;
+    double* fb = out + (long long)o * ostride + col0;
     double* cur = raw + (nbuf == 2 ? b : 0) * bstride;
     if (nbuf == 1) issue(o, cur);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -306,9 +306,11 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
 template <int N, bool IN_DF, bool OUT_DF>
 cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st) {
   double* f = reinterpret_cast<double*>(a.f);
+  double* out = reinterpret_cast<double*>(a.out ? a.out : a.f);
   const float2* ab2 = reinterpret_cast<const float2*>(a.ab2);
   const long long D = (long long)a.nc * N;
   const bool percol = a.dim >= 2;
+  if (reinterpret_cast<uintptr_t>(out) & 15) return cudaErrorNotSupported;
   if (!percol && !a.periodic) return cudaErrorNotSupported;
   long long ncols, rstride, ostride, outer;
   if (a.dim == 3) {
@@ -350,7 +352,7 @@ cudaError_t launch_strided_df3_T(const SweepArgs& a, cudaStream_t st) {
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
-  kfn<<<grid, kDf3Threads, smem, st>>>(f, (int)ncols, rstride, ostride, a.nc, (int)outer, nbuf, ab2,
+  kfn<<<grid, kDf3Threads, smem, st>>>(f, out, (int)ncols, rstride, ostride, a.nc, (int)outer, nbuf, ab2,
                                        a.s, a.mcount, (int)a.key_div, (int)a.key_mod);
   return cudaGetLastError();
 }
@@ -679,26 +681,33 @@ cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st) {
 // a fixed order.
 // ---------------------------------------------------------------------------
 template <int N>
-inline size_t ebar_df3_smem(long long D) {
-  return (size_t)kDf3Pairs * df3_mat_stride<N>() * sizeof(float4) +
+inline size_t ebar_df3_smem(long long D, bool fuse = false) {
+  return (fuse ? 2 : 1) * (size_t)kDf3Pairs * df3_mat_stride<N>() * sizeof(float4) +
          2 * (size_t)(D + N) * kStridedW * sizeof(double) +
          (size_t)kDf3Groups * kStridedW * sizeof(double);
 }
 
-template <int N, bool PERIODIC>
+// G_DF: the forward input gf holds double-float pairs instead of doubles.
+// FUSE: the same CTA then applies the transposed sweep to the staged adjoint
+// tile (forward form on the transposed tables tab2 / tsvec: [B^T; A^T],
+// shifts -s - 1) and writes it back to lam, so the adjoint is read once for
+// both.
+template <int N, bool PERIODIC, bool G_DF, bool FUSE>
 __global__ void __launch_bounds__(kDf3Threads, 2)
-    k_ebar_df3(const double* __restrict__ lam, const double* __restrict__ gf,
+    k_ebar_df3(double* lam, const double* __restrict__ gf,
                double* __restrict__ epart, int ncols, long long rstride, long long ostride, int nc,
                int outer, const float2* __restrict__ dab2, const int* __restrict__ svec,
-               long long mcount) {
+               long long mcount, const float2* __restrict__ tab2, const int* __restrict__ tsvec) {
   constexpr int W = kStridedW;
   constexpr int MN = 2 * N * N;
   constexpr int MS = df3_mat_stride<N>();
   extern __shared__ __align__(16) unsigned char smraw[];
   float4* smat = reinterpret_cast<float4*>(smraw);
+  float4* tmat = smat + (FUSE ? kDf3Pairs * MS : 0);  // transposed tables (FUSE)
   const int D = nc * N;
   const int bstride = (D + N) * W;
-  double* tl = reinterpret_cast<double*>(smraw + (size_t)kDf3Pairs * MS * sizeof(float4));
+  double* tl = reinterpret_cast<double*>(smraw + (size_t)(FUSE ? 2 : 1) * kDf3Pairs * MS *
+                                                      sizeof(float4));
   double* tg = tl + bstride;
   double* red = tg + bstride;  // [groups][W]
   const int col0 = blockIdx.x * W;
@@ -713,15 +722,29 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
     const int k0 = min(col0 + 2 * pq, ncols - 1), k1 = min(col0 + 2 * pq + 1, ncols - 1);
     const float2 a0 = dab2[(long long)i * mcount + k0], a1 = dab2[(long long)i * mcount + k1];
     smat[pq * MS + i] = make_float4(a0.x, a1.x, a0.y, a1.y);
+    if (FUSE) {
+      const float2 b0 = tab2[(long long)i * mcount + k0], b1 = tab2[(long long)i * mcount + k1];
+      tmat[pq * MS + i] = make_float4(b0.x, b1.x, b0.y, b1.y);
+    }
   }
   int sa0 = -svec[min(col0 + c0, ncols - 1)] - 1;
   int sa1 = -svec[min(col0 + c0 + 1, ncols - 1)] - 1;
+  int ta0 = 0, ta1 = 0;  // a-cell offsets of the transposed sweep
+  if (FUSE) {
+    ta0 = -tsvec[min(col0 + c0, ncols - 1)] - 1;
+    ta1 = -tsvec[min(col0 + c0 + 1, ncols - 1)] - 1;
+  }
   if (PERIODIC) {
     sa0 = wrap_cell(sa0, nc);
     sa1 = wrap_cell(sa1, nc);
+    ta0 = wrap_cell(ta0, nc);
+    ta1 = wrap_cell(ta1, nc);
   }
   if (!PERIODIC)
-    for (int i = threadIdx.x; i < N * W; i += blockDim.x) tg[D * W + i] = 0.0;
+    for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
+      tg[D * W + i] = 0.0;
+      if (FUSE) tl[D * W + i] = 0.0;  // the zero-inflow cell of the transposed sweep
+    }
   const float4* M = smat + q * MS;
   const int chunks = D * (W / 2);
   const int vchunks = nvalid / 2;
@@ -741,7 +764,7 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
     cp_async_wait_all();
     __syncthreads();
     df3_pair_planar<false>(tl, D * (W / 2));
-    df3_pair_planar<false>(tg, D * (W / 2));
+    df3_pair_planar<G_DF>(tg, D * (W / 2));
     __syncthreads();
     float2 ph = make_float2(0.0f, 0.0f), pl = make_float2(0.0f, 0.0f);  // per-lane partial
     bool first = true;
@@ -778,6 +801,11 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
         }
       }
     }
+    if (FUSE && active) {  // the transposed sweep from the staged adjoint, to lam
+      const float4* MT = tmat + q * MS;
+      if (ta0 == ta1) df3_run<N, PERIODIC, true, false>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
+      else df3_run<N, PERIODIC, false, false>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
+    }
     red[g * W + c0] = djoin_fast(ph.x, pl.x);
     red[g * W + c0 + 1] = djoin_fast(ph.y, pl.y);
     __syncthreads();
@@ -790,11 +818,14 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
   }
 }
 
+// a.tab2, a.ts non-null: the fused form (partials, then the transposed sweep
+// of the adjoint in place from the same staged tile)
 template <int N>
 cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
-  const double* lam = reinterpret_cast<const double*>(a.f);
+  double* lam = reinterpret_cast<double*>(a.f);
   const double* gf = reinterpret_cast<const double*>(a.g);
   const long long D = (long long)a.nc * N;
+  const bool fuse = a.tab2 && a.ts;
   long long ncols, rstride, ostride, outer;
   if (a.dim == 3) {
     ncols = a.key_mod;
@@ -813,17 +844,23 @@ cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
       ((reinterpret_cast<uintptr_t>(lam) | reinterpret_cast<uintptr_t>(gf)) & 15) ||
       ncols > 0x7fffffffLL - kStridedW || outer > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
     return cudaErrorNotSupported;
-  const size_t smem = ebar_df3_smem<N>(D);
+  const size_t smem = ebar_df3_smem<N>(D, fuse);
   if (smem > 113 * 1024) return cudaErrorNotSupported;
   const long long ncolblk = (ncols + kStridedW - 1) / kStridedW;
   long long gy = (outer + kDf3TilesPerCtaV - 1) / kDf3TilesPerCtaV;
   if (gy > 65535) gy = 65535;
-  auto kfn = a.periodic ? k_ebar_df3<N, true> : k_ebar_df3<N, false>;
+  auto pick = [&](auto fuse_t) {
+    constexpr bool F = decltype(fuse_t)::value;
+    return a.periodic ? (a.g_df ? k_ebar_df3<N, true, true, F> : k_ebar_df3<N, true, false, F>)
+                      : (a.g_df ? k_ebar_df3<N, false, true, F> : k_ebar_df3<N, false, false, F>);
+  };
+  auto kfn = fuse ? pick(std::true_type()) : pick(std::false_type());
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   kfn<<<dim3((unsigned)ncolblk, (unsigned)gy), kDf3Threads, smem, st>>>(
       lam, gf, a.epart, (int)ncols, rstride, ostride, a.nc, (int)outer,
-      reinterpret_cast<const float2*>(a.dab2), a.s, a.mcount);
+      reinterpret_cast<const float2*>(a.dab2), a.s, a.mcount,
+      reinterpret_cast<const float2*>(a.tab2), a.ts);
   return cudaGetLastError();
 }
 

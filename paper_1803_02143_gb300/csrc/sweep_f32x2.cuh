@@ -97,7 +97,7 @@ __device__ __forceinline__ void f2_run(const float* __restrict__ t, const float2
 // (key = (o / key_div) % key_mod, contiguous outer indices per CTA).
 template <int N, bool PERIODIC, bool PERCOL>
 __global__ void __launch_bounds__(kF2Threads, 2)
-    k_sweep_strided_f2(float* __restrict__ f, int ncols, long long rstride, long long ostride,
+    k_sweep_strided_f2(const float* f, float* out, int ncols, long long rstride, long long ostride,
                        int nc, int outer, const float* __restrict__ ab,
                        const int* __restrict__ svec, long long mcount, int key_div, int key_mod) {
   constexpr int W = kF2W;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kF2Threads, 2)
   if (o0 < o1) issue(o0, raw);
   int b = 0;
   for (int o = o0; o < o1; o += ostep, b ^= 1) {
-    float* fb = f + (long long)o * ostride + col0;
+    float* fb = out + (long long)o * ostride + col0;
     const float* cur = raw + b * bstride;
     if (!PERCOL) {
       const int key = (o / key_div) % key_mod;
@@ -187,9 +187,11 @@ __global__ void __launch_bounds__(kF2Threads, 2)
 template <int N>
 cudaError_t launch_strided_f2_T(const SweepArgs& a, cudaStream_t st) {
   float* f = reinterpret_cast<float*>(a.f);
+  float* out = reinterpret_cast<float*>(a.out ? a.out : a.f);
   const long long D = (long long)a.nc * N;
   const bool percol = a.dim >= 2;
   if (!percol && !a.periodic) return cudaErrorNotSupported;
+  if (reinterpret_cast<uintptr_t>(out) & 15) return cudaErrorNotSupported;
   long long ncols, rstride, ostride, outer;
   if (a.dim == 3) {
     ncols = a.key_mod;
@@ -219,7 +221,7 @@ cudaError_t launch_strided_f2_T(const SweepArgs& a, cudaStream_t st) {
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   kfn<<<dim3((unsigned)ncolblk, (unsigned)gy), kF2Threads, smem, st>>>(
-      f, (int)ncols, rstride, ostride, a.nc, (int)outer, reinterpret_cast<const float*>(a.ab), a.s,
+      f, out, (int)ncols, rstride, ostride, a.nc, (int)outer, reinterpret_cast<const float*>(a.ab), a.s,
       a.mcount, (int)a.key_div, (int)a.key_mod);
   return cudaGetLastError();
 }
@@ -344,7 +346,7 @@ cudaError_t launch_x1_f2warp_T(const SweepArgs& a, cudaStream_t st) {
 
 template <int N>
 cudaError_t launch_sweep_f2_N(const SweepArgs& a, cudaStream_t st) {
-  if (a.adjoint) return cudaErrorNotSupported;
+  if (a.adjoint || (a.dim == 0 && out_of_place(a))) return cudaErrorNotSupported;
   return a.dim == 0 ? launch_x1_f2warp_T<N>(a, st) : launch_strided_f2_T<N>(a, st);
 }
 

@@ -5,6 +5,7 @@
 namespace sldg {
 
 cudaError_t launch_sweep_f64(const SweepArgs& a, cudaStream_t st) {
+  if (out_of_place(a)) return cudaErrorNotSupported;  // in place only
   return launch_sweep_any<PolF64>(a, st);
 }
 

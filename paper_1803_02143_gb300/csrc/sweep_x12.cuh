@@ -64,7 +64,7 @@ __host__ __device__ __forceinline__ int x12_lanes_per_pair(int nc0, int cpl) {
 // groups per warp in the X1 phase (lines of at most 16 CPL cells)
 template <int N, int CPL, bool GRP>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
-    k_sweep_x12_f32(float* __restrict__ f, int nc0, int nc1, int cs, int D2, int D3,
+    k_sweep_x12_f32(const float* src, float* dst, int nc0, int nc1, int cs, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
                     const float* __restrict__ ab2, const int* __restrict__ s2) {
   constexpr int NN = N * N;
@@ -75,14 +75,15 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
   const long long plane = blockIdx.x / cs;
   const int cells_per = nc1 / cs;  // x2 cells held by one CTA
   const int H = cells_per * N;     // rows held by one CTA
-  float* fp = f + plane * (long long)D1 * D0;
+  const float* fp = src + plane * (long long)D1 * D0;  // read
+  float* op = dst + plane * (long long)D1 * D0;        // written (may be fp)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
   // 1. stage rows rank*H .. rank*H + H - 1
   {
-    const float* src = fp + (long long)rank * H * D0;
+    const float* sp = fp + (long long)rank * H * D0;
     const int chunks = H * D0 / 4;
-    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 4 * i, src + 4 * i);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 4 * i, sp + 4 * i);
     cp_async_wait_all();
   }
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       if (k >= nc1) k -= nc1;
       float2 xa[N], xb[N];
       load(k, c0, xa);
-      float* out = fp + (long long)(cglob * N) * D0 + c0;
+      float* out = op + (long long)(cglob * N) * D0 + c0;
 #pragma unroll 1
       for (int c = lb; c < le; ++c, out += N * D0) {
         k = k + 1 == nc1 ? 0 : k + 1;
@@ -194,12 +195,13 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
 // Fused X1(frac) X2(frac) on FP32 storage; cudaErrorNotSupported when the
 // layout does not fit (the caller then runs the two sweeps).
 template <int N, int CPL>
-cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
-                         const int* s2, cudaStream_t st, int* shape) {
+cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
   const long long planes = g.D[2] * g.D[3];
-  if (D0 % 4 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
+  if (D0 % 4 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
+    return cudaErrorNotSupported;
   // the smallest cluster (a single CTA when the plane fits) whose row share
   // fits three CTAs per SM
   int cs = 0;
@@ -234,16 +236,16 @@ cudaError_t launch_x12_T(float* f, const Grid& g, const void* ab1, const int* s1
     shape[0] = cs;
     shape[1] = x12_lanes_per_pair(nc0, CPL);
   }
-  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
+  return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
                             static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2);
 }
 
 template <int N>
-cudaError_t launch_x12_N(float* f, const Grid& g, const void* ab1, const int* s1, const void* ab2,
-                         const int* s2, cudaStream_t st, int* shape) {
+cudaError_t launch_x12_N(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0];
-  if (nc0 <= 64) return launch_x12_T<N, 2>(f, g, ab1, s1, ab2, s2, st, shape);
-  if (nc0 <= 128) return launch_x12_T<N, 4>(f, g, ab1, s1, ab2, s2, st, shape);
+  if (nc0 <= 64) return launch_x12_T<N, 2>(f, out, g, ab1, s1, ab2, s2, st, shape);
+  if (nc0 <= 128) return launch_x12_T<N, 4>(f, out, g, ab1, s1, ab2, s2, st, shape);
   return cudaErrorNotSupported;
 }
 

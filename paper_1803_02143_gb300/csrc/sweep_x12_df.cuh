@@ -38,7 +38,7 @@ __device__ __forceinline__ float4 ld_cluster_f4(unsigned addr) {
 // run: consecutive x2 cells of one X2 work item (one column pair)
 template <int N, int CPL, bool GRP, bool IN_DF, bool OUT_DF>
 __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
-    k_sweep_x12_df(double* __restrict__ f, int nc0, int nc1, int cs, int run, int D2, int D3,
+    k_sweep_x12_df(const double* src, double* dst, int nc0, int nc1, int cs, int run, int D2, int D3,
                    const float2* __restrict__ ab1, const int* __restrict__ s1,
                    const float2* __restrict__ ab2, const int* __restrict__ s2) {
   constexpr int MN = 2 * N * N;
@@ -51,13 +51,14 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
   const long long plane = blockIdx.x / cs;
   const int cells_per = nc1 / cs;
   const int H = cells_per * N;
-  double* fp = f + plane * (long long)D1 * D0;
+  const double* fp = src + plane * (long long)D1 * D0;  // read
+  double* op = dst + plane * (long long)D1 * D0;        // written (may be fp)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
   {
-    const double* src = fp + (long long)rank * H * D0;
+    const double* sp = fp + (long long)rank * H * D0;
     const int chunks = H * D0 / 2;
-    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 2 * i, src + 2 * i);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 2 * i, sp + 2 * i);
   }
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
   for (int i = threadIdx.x; i < MN; i += blockDim.x) {
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
         if (local != (pass == 0)) continue;
         const int cglob = (int)rank * cells_per + lb;
         float2 ah[N], al[N], bh[N], bl[N];
-        double* out = fp + (long long)(cglob * N) * D0 + c0;
+        double* out = op + (long long)(cglob * N) * D0 + c0;
         if (local) {
           int k = lb + d;
           local_load(k, c0, ah, al);
@@ -206,12 +207,14 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
 }
 
 template <int N, int CPL, bool IN_DF, bool OUT_DF>
-cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int* s1,
-                            const void* ab2, const int* s2, cudaStream_t st, int* shape) {
+cudaError_t launch_x12_df_T(const double* f, double* out, const Grid& g, const void* ab1,
+                            const int* s1, const void* ab2, const int* s2, cudaStream_t st,
+                            int* shape) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N;
   const long long planes = g.D[2] * g.D[3];
-  if (D0 % 2 || (reinterpret_cast<uintptr_t>(f) & 15)) return cudaErrorNotSupported;
+  if (D0 % 2 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
+    return cudaErrorNotSupported;
   const size_t mats = 2 * (size_t)(2 * N * N) * sizeof(float4);
   // the smallest cluster (2 to 8 CTAs) whose row share fits six CTAs per SM,
   // else the largest that fits one
@@ -251,16 +254,17 @@ cudaError_t launch_x12_df_T(double* f, const Grid& g, const void* ab1, const int
     shape[0] = cs;
     shape[1] = x12_lanes_per_pair(nc0, CPL);
   }
-  return cudaLaunchKernelEx(&cfg, kfn, f, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
+  return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
                             static_cast<const float2*>(ab1), s1, static_cast<const float2*>(ab2),
                             s2);
 }
 
 template <int N, bool IN_DF, bool OUT_DF>
-cudaError_t launch_x12_df_N(double* f, const Grid& g, const void* ab1, const int* s1,
-                            const void* ab2, const int* s2, cudaStream_t st, int* shape) {
+cudaError_t launch_x12_df_N(const double* f, double* out, const Grid& g, const void* ab1,
+                            const int* s1, const void* ab2, const int* s2, cudaStream_t st,
+                            int* shape) {
   if (g.nc[0] <= 64)
-    return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, g, ab1, s1, ab2, s2, st, shape);
+    return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, out, g, ab1, s1, ab2, s2, st, shape);
   return cudaErrorNotSupported;
 }
 
