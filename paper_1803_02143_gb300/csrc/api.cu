@@ -169,7 +169,7 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_ckpool); dfree(c->d_seg); dfree(c->d_Ecap);
   for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
   dfree(c->d_alt);
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
     c->step_graph[i] = nullptr;
   }
@@ -231,7 +231,7 @@ bool df_states(const sldg_ctx* c) {
 }
 
 void drop_step_graphs(sldg_ctx* c) {
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
     c->step_graph[i] = nullptr;
   }
@@ -470,13 +470,11 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // commute like X1 and X2), run in forward form on the transposed tables
 // ([B^T; A^T], shift entries -s - 1) like the separate adjoint x-sweeps
 // out (nullable): the result goes there and buf is left unchanged
-// twice: the drift two times in a row in one pass (FP32 storage only)
 int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done,
-            bool trans = false, void* out = nullptr, bool twice = false) {
+            bool trans = false, void* out = nullptr) {
   *done = false;
   if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE))
     return SLDG_OK;
-  if (twice && c->prec != SLDG_FP32) return SLDG_OK;
   MatSet *m0, *m1;
   SLDG_TRY(ensure_xmats(c, 0, frac, trans, &m0));
   SLDG_TRY(ensure_xmats(c, 1, frac, trans, &m1));
@@ -486,8 +484,7 @@ int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* 
   const cudaError_t e =
       c->prec == SLDG_FP32
           ? launch_sweep_x12_f32(buf, c->g, trans ? m0->abt : m0->ab, s0,
-                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape, out,
-                                 twice)
+                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape, out)
           : launch_sweep_x12_df(buf, c->g, trans ? m0->abt2 : m0->ab2, s0,
                                 trans ? m1->abt2 : m1->ab2, s1, in_df ? 1 : 0, out_df ? 1 : 0,
                                 c->stream, c->x12_shape, out);
@@ -521,17 +518,6 @@ int drift(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, void* ou
   return SLDG_OK;
 }
 
-// The drift X1 X2 (frac tau) two times in a row on FP32 storage: one pass
-// over each x-plane where the layout allows it (the same arithmetic as two
-// passes), else two drifts.
-int drift2(sldg_ctx* c, void* buf, double frac) {
-  bool fused = false;
-  SLDG_TRY(run_x12(c, buf, frac, false, false, &fused, false, nullptr, true));
-  if (fused) return SLDG_OK;
-  SLDG_TRY(drift(c, buf, frac, false, false));
-  return drift(c, buf, frac, false, false);
-}
-
 // ---- splitting compositions -------------------------------------------------------
 // A step is a list of stages: drifts (X1 X2 by frac tau) and kicks (the
 // field of the current rho, then V1 V2 by frac tau).  Order 2 is the Strang
@@ -544,8 +530,6 @@ struct Stage {
   bool kick;
   bool W;  // the first kick of a step: W of its field is recorded
   double frac;
-  bool twice = false;  // a drift applied two times in a row (the last of one
-                       // Strang step and the first of the next)
 };
 
 int strang_weights(const sldg_ctx* c, double* w) {
@@ -588,24 +572,6 @@ std::vector<Stage> merged_body(const sldg_ctx* c, bool last) {
   return st;
 }
 
-// Paired drifts (FP32 storage, plain Strang steps): the last half drift of a
-// step and the first of the next are the same drift X(1/2) twice in a row,
-// which one pass over each x-plane applies (bit for bit the separate
-// drifts); a call of n >= 2 steps is D(1/2), n - 1 bodies K(1) D(1/2)D(1/2),
-// and K(1) D(1/2).
-bool paired(const sldg_ctx* c) {
-  return c->prec == SLDG_FP32 &&
-         !(c->cfg.flags & (SLDG_FLAG_ORDER4 | SLDG_FLAG_MERGE_DRIFTS | SLDG_FLAG_SPLINE |
-                           SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64));
-}
-
-std::vector<Stage> paired_body(bool last) {
-  std::vector<Stage> st;
-  st.push_back({true, true, 1.0});
-  st.push_back({false, false, 0.5, !last});
-  return st;
-}
-
 // Run stages in place on buf.  FP64 storage with double-float sweeps: buf
 // holds IEEE doubles where in_ieee / out_ieee say so (the call's first
 // input, its last output) and double-float (hi, lo) pairs in the same
@@ -621,10 +587,6 @@ int run_stages(sldg_ctx* c, void* buf, const std::vector<Stage>& st, bool in_iee
     const bool in_df = df && (q > 0 || !in_ieee);
     const bool out_df = df && (q + 1 < n || !out_ieee);
     if (!st[q].kick) {
-      if (st[q].twice) {
-        SLDG_TRY(drift2(c, buf, st[q].frac));
-        continue;
-      }
       SLDG_TRY(drift(c, buf, st[q].frac, in_df, out_df));
       continue;
     }
@@ -691,28 +653,22 @@ int forward_stage(sldg_ctx* c, const void* src, void* g2_out, void* g3_out, doub
   return drift(c, dst, 0.5, df, false);
 }
 
-// The repeated unit of sldg_step: a whole step (IEEE in and out), or
-// (chained) the body of a step that another step follows: with merged
-// drifts (double-float pairs in and out on FP64 storage), or with paired
-// drifts.
-int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter, bool chained) {
+// The repeated unit of sldg_step: a whole step (IEEE in and out), or with
+// merged drifts the body of a step that another step follows (double-float
+// pairs in and out on FP64 storage).
+int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter) {
   int wi = 0;
-  if (chained && merged(c))
-    return run_stages(c, buf, merged_body(c, false), false, false, Wslot, Wcounter, &wi);
-  if (chained) return run_stages(c, buf, paired_body(false), false, false, Wslot, Wcounter, &wi);
+  if (merged(c)) return run_stages(c, buf, merged_body(c, false), false, false, Wslot, Wcounter, &wi);
   return run_stages(c, buf, step_stages(c), true, true, Wslot, Wcounter, &wi);
 }
 
-// nsteps units of f (whole steps, or chained bodies) as replays of one
-// recorded unit (a CUDA graph), W of
+// nsteps units of f as replays of one recorded unit (a CUDA graph), W of
 // each to Wbase[counter++] (nullable; the device counter restarts at 0 when
 // reset_counter).  *replayed stays false when graphs do not apply (fewer
 // than two units, per-kernel timing on, or an earlier capture failed) and
 // the caller runs the units eagerly.
-int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed,
-                 bool chained = false) {
+int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed) {
   const int hv = Wbase ? 1 : 0;
-  const int k = hv + (chained ? 2 : 0);  // graph slot: unit kind, W history or not
   *replayed = false;
   if (nsteps >= 2 && !c->timing && !c->graphs_off) {
     // one recorded step replayed nsteps times: the launch overhead of the
@@ -721,37 +677,37 @@ int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, boo
     SLDG_TRY(prepare_xmats(c));
     for (int d = 0; d < 2; ++d) SLDG_TRY(alloc_matset(c, &c->vm[d], c->g.Dx, false, false));
     if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
-    if (c->step_graph[k] && (c->step_graph_buf[k] != c->f || c->step_graph_W[k] != Wbase)) {
-      cudaGraphExecDestroy(c->step_graph[k]);
-      c->step_graph[k] = nullptr;
+    if (c->step_graph[hv] && (c->step_graph_buf[hv] != c->f || c->step_graph_W[hv] != Wbase)) {
+      cudaGraphExecDestroy(c->step_graph[hv]);
+      c->step_graph[hv] = nullptr;
     }
-    if (!c->step_graph[k]) {
+    if (!c->step_graph[hv]) {
       const long long l0 = c->launches;
       cudaGraph_t graph = nullptr;
       bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      const int rc = ok ? run_unit(c, c->f, Wbase, hv ? c->d_counter : nullptr, chained) : SLDG_ERR_CUDA;
+      const int rc = ok ? run_unit(c, c->f, Wbase, hv ? c->d_counter : nullptr) : SLDG_ERR_CUDA;
       if (ok) ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && rc == SLDG_OK;
-      if (ok) ok = cudaGraphInstantiate(&c->step_graph[k], graph, 0) == cudaSuccess;
+      if (ok) ok = cudaGraphInstantiate(&c->step_graph[hv], graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
-      c->step_graph_launches[k] = c->launches - l0;
+      c->step_graph_launches[hv] = c->launches - l0;
       c->launches = l0;
       if (!ok) {
         cudaGetLastError();
-        if (c->step_graph[k]) cudaGraphExecDestroy(c->step_graph[k]);
-        c->step_graph[k] = nullptr;
+        if (c->step_graph[hv]) cudaGraphExecDestroy(c->step_graph[hv]);
+        c->step_graph[hv] = nullptr;
         c->graphs_off = true;
         invalidate_vmats(c);
         c->have_field = false;
       } else {
-        c->step_graph_buf[k] = c->f;
-        c->step_graph_W[k] = Wbase;
+        c->step_graph_buf[hv] = c->f;
+        c->step_graph_W[hv] = Wbase;
       }
     }
-    if (c->step_graph[k]) {
+    if (c->step_graph[hv]) {
       if (hv && reset_counter) SLDG_CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
       for (int m = 0; m < nsteps; ++m) {
-        SLDG_CU(cudaGraphLaunch(c->step_graph[k], c->stream));
-        c->launches += c->step_graph_launches[k];
+        SLDG_CU(cudaGraphLaunch(c->step_graph[hv], c->stream));
+        c->launches += c->step_graph_launches[hv];
         c->t += c->g.dt;
         c->step += 1;
       }
@@ -1019,29 +975,27 @@ int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
   if (nsteps < 0) return SLDG_ERR_ARG;
   if (W_history) SLDG_TRY(ensure_W(c, nsteps));
   double* Wd = W_history ? c->d_W : nullptr;
-  // chained steps (merged or paired drifts): the first drift, nsteps - 1
-  // bodies (replayed), the last body
+  // merged drifts: D(w_0/2), nsteps - 1 bodies (replayed), the last body
   const bool mg = merged(c) && nsteps > 0;
-  const bool ch = mg || (paired(c) && nsteps >= 2);
-  const int units = ch ? nsteps - 1 : nsteps;
-  if (ch) {
+  const int units = mg ? nsteps - 1 : nsteps;
+  if (mg) {
     double w[3];
     strang_weights(c, w);
     int wi = 0;
     SLDG_TRY(run_stages(c, c->f, {{false, false, 0.5 * w[0]}}, true, false, nullptr, nullptr, &wi));
   }
   bool replayed = false;
-  SLDG_TRY(replay_steps(c, units, Wd, true, &replayed, ch));
+  SLDG_TRY(replay_steps(c, units, Wd, true, &replayed));
   if (!replayed)
     for (int m = 0; m < units; ++m) {
-      SLDG_TRY(run_unit(c, c->f, Wd ? Wd + m : nullptr, nullptr, ch));
+      SLDG_TRY(run_unit(c, c->f, Wd ? Wd + m : nullptr, nullptr));
       c->t += c->g.dt;
       c->step += 1;
     }
-  if (ch) {
+  if (mg) {
     int wi = 0;
-    SLDG_TRY(run_stages(c, c->f, mg ? merged_body(c, true) : paired_body(true), false, true,
-                        Wd ? Wd + units : nullptr, nullptr, &wi));
+    SLDG_TRY(run_stages(c, c->f, merged_body(c, true), false, true, Wd ? Wd + units : nullptr,
+                        nullptr, &wi));
     c->t += c->g.dt;
     c->step += 1;
   }

@@ -84,11 +84,10 @@ cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 // fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the
 // layout does not fit.  shape (nullable, two ints): the launch's CTAs per
 // x-plane (cluster size) and lanes per x1 line pair of its X1 phase.  out
-// (nullable): write the result there and leave f unchanged.  twice: the
-// drift two times in a row in one pass (FP32 only).
+// (nullable): write the result there and leave f unchanged.
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
                                  const void* ab2, const int* s2, cudaStream_t st,
-                                 int* shape = nullptr, void* out = nullptr, bool twice = false);
+                                 int* shape = nullptr, void* out = nullptr);
 // the same for FP64 storage in double-float arithmetic (sweep_df.cu); ab1, ab2
 // are the (hi, lo) float-pair tables, in_df / out_df the element formats
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
@@ -182,11 +181,10 @@ struct sldg_ctx {
   // sldg_step as a replayed CUDA graph of one step (two variants: without /
   // with the W history, whose slot comes from a device counter); with merged
   // drifts the graph holds the part of a step between two merged drifts
-  // [W history or not + 2 * chained body (merged or paired drifts)]
-  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
-  const void* step_graph_buf[4] = {nullptr, nullptr, nullptr, nullptr};  // f and W history they were made for
-  const void* step_graph_W[4] = {nullptr, nullptr, nullptr, nullptr};
-  long long step_graph_launches[4] = {0, 0, 0, 0};
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  const void* step_graph_buf[2] = {nullptr, nullptr};  // f and W history they were made for
+  const void* step_graph_W[2] = {nullptr, nullptr};
+  long long step_graph_launches[2] = {0, 0};
   bool graphs_off = false;  // a capture failed: steps run eagerly from then on
   int* d_counter = nullptr;
 

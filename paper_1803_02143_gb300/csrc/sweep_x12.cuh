@@ -61,26 +61,20 @@ __host__ __device__ __forceinline__ int x12_lanes_per_pair(int nc0, int cpl) {
 }
 
 // CPL: cells of an x1 line per lane (nc0 <= 32 CPL); GRP: several lane
-// groups per warp in the X1 phase (lines of at most 16 CPL cells).
-// TWICE: two consecutive drifts X1 X2 X1 X2 by the same fraction (the last
-// half drift of a Strang step and the first of the next) in one pass: the
-// first X2 writes into a second row buffer of the CTA instead of f, the
-// second X1 runs on that buffer, and only the second X2 writes f.  The
-// arithmetic of every output is that of two single passes.
-template <int N, int CPL, bool GRP, bool TWICE>
+// groups per warp in the X1 phase (lines of at most 16 CPL cells)
+template <int N, int CPL, bool GRP>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     k_sweep_x12_f32(const float* src, float* dst, int nc0, int nc1, int cs, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
                     const float* __restrict__ ab2, const int* __restrict__ s2) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smraw[];
+  float* rows = reinterpret_cast<float*>(smraw);
   const int D0 = nc0 * N, D1 = nc1 * N;
   const unsigned rank = cluster_ctarank();
   const long long plane = blockIdx.x / cs;
   const int cells_per = nc1 / cs;  // x2 cells held by one CTA
   const int H = cells_per * N;     // rows held by one CTA
-  float* rows = reinterpret_cast<float*>(smraw);
-  float* rows2 = rows + (TWICE ? H * D0 : 0);  // second buffer (TWICE)
   const float* fp = src + plane * (long long)D1 * D0;  // read
   float* op = dst + plane * (long long)D1 * D0;        // written (may be fp)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -95,10 +89,10 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
   __syncthreads();
 
-  // 2. X1 in place on buf, a group of lpp lanes per row pair (the two lanes
-  //    of every FP32x2 op are the pair's two rows); short lines put several
-  //    groups in one warp
-  auto x1 = [&](float* buf) {
+  // 2. X1 in place, a group of lpp lanes per row pair (the two lanes of every
+  //    FP32x2 op are the pair's two rows); short lines put several groups in
+  //    one warp
+  {
     float2 A[NN], B[NN];
 #pragma unroll
     for (int i = 0; i < NN; ++i) {
@@ -112,7 +106,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     const unsigned gmask = GRP ? ((1u << lpp) - 1) << (grp * lpp) : 0xffffffffu;
     const int cb = min(gl * CPL, nc0), ce = min(cb + CPL, nc0);
     for (int p = wid * G + grp; p < H / 2; p += nw * G) {
-      float* ra = buf + (2 * p) * D0;
+      float* ra = rows + (2 * p) * D0;
       float* rb = ra + D0;
       float2 x[CPL + 1][N];
       int k = cb + sa;
@@ -141,13 +135,12 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       }
       __syncwarp(gmask);
     }
-  };
+  }
+  // 3. every CTA's rows hold X1 f
+  cluster_sync();
 
-  // 4. X2 for rows rank*H .. rank*H + H - 1 from buf: the source rows of an
-  //    output cell (periodic in x2) come from this CTA's buf or, across the
-  //    row split, from the owning CTA's; outputs to f, or (local non-null)
-  //    to the same rows of this CTA's buffer `local`
-  auto x2 = [&](const float* buf, float* local) {
+  // 4. X2 for rows rank*H .. rank*H + H - 1
+  {
     float2 A[NN], B[NN];
 #pragma unroll
     for (int i = 0; i < NN; ++i) {
@@ -164,9 +157,9 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       if (owner == (int)rank) {
 #pragma unroll
         for (int l = 0; l < N; ++l)
-          xv[l] = *reinterpret_cast<const float2*>(buf + (lrow + l) * D0 + c0);
+          xv[l] = *reinterpret_cast<const float2*>(rows + (lrow + l) * D0 + c0);
       } else {
-        const unsigned base = cluster_map(buf + lrow * D0 + c0, (unsigned)owner);
+        const unsigned base = cluster_map(rows + lrow * D0 + c0, (unsigned)owner);
 #pragma unroll
         for (int l = 0; l < N; ++l) xv[l] = ld_cluster_f2(base + (unsigned)(l * D0 * 4));
       }
@@ -181,7 +174,7 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       if (k >= nc1) k -= nc1;
       float2 xa[N], xb[N];
       load(k, c0, xa);
-      float* out = local ? local + (long long)(lb * N) * D0 + c0 : op + (long long)(cglob * N) * D0 + c0;
+      float* out = op + (long long)(cglob * N) * D0 + c0;
 #pragma unroll 1
       for (int c = lb; c < le; ++c, out += N * D0) {
         k = k + 1 == nc1 ? 0 : k + 1;
@@ -194,52 +187,37 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
         for (int l = 0; l < N; ++l) xa[l] = xb[l];
       }
     }
-  };
-
-  x1(rows);
-  cluster_sync();  // 3. every CTA's rows hold X1 f
-  if (TWICE) {
-    x2(rows, rows2);
-    __syncthreads();  // this CTA's second buffer holds X2 X1 f
-    x1(rows2);
-    cluster_sync();  // every CTA's second buffer holds X1 X2 X1 f
-    x2(rows2, nullptr);
-  } else {
-    x2(rows, nullptr);
   }
   // 5. peers may still read these rows
   cluster_sync();
 }
 
-// Fused X1(frac) X2(frac) on FP32 storage (twice: that drift two times in a
-// row); cudaErrorNotSupported when the layout does not fit (the caller then
-// runs the sweeps).
+// Fused X1(frac) X2(frac) on FP32 storage; cudaErrorNotSupported when the
+// layout does not fit (the caller then runs the two sweeps).
 template <int N, int CPL>
 cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
-                         const void* ab2, const int* s2, cudaStream_t st, int* shape, bool twice) {
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 4 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
     return cudaErrorNotSupported;
   // the smallest cluster (a single CTA when the plane fits) whose row share
-  // (two buffers of it for twice) fits three CTAs per SM
-  const int nbuf = twice ? 2 : 1;
+  // fits three CTAs per SM
   int cs = 0;
   for (int c = 1; c <= 8; c *= 2) {
     if (nc1 % c) continue;
     const long long H = (long long)(nc1 / c) * N;
     if (H % 2 || (H * D0) % 4) continue;
-    if (nbuf * H * D0 * (long long)sizeof(float) <= 75 * 1024) {
+    if (H * D0 * (long long)sizeof(float) <= 75 * 1024) {
       cs = c;
       break;
     }
   }
   if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
-  const size_t smem = (size_t)nbuf * (nc1 / cs) * N * D0 * sizeof(float);
-  const bool grp = x12_lanes_per_pair(nc0, CPL) < 32;
-  auto kfn = twice ? (grp ? k_sweep_x12_f32<N, CPL, true, true> : k_sweep_x12_f32<N, CPL, false, true>)
-                   : (grp ? k_sweep_x12_f32<N, CPL, true, false> : k_sweep_x12_f32<N, CPL, false, false>);
+  const size_t smem = (size_t)(nc1 / cs) * N * D0 * sizeof(float);
+  auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_f32<N, CPL, true>
+                                               : k_sweep_x12_f32<N, CPL, false>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -264,10 +242,10 @@ cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* 
 
 template <int N>
 cudaError_t launch_x12_N(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
-                         const void* ab2, const int* s2, cudaStream_t st, int* shape, bool twice) {
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
   const int nc0 = g.nc[0];
-  if (nc0 <= 64) return launch_x12_T<N, 2>(f, out, g, ab1, s1, ab2, s2, st, shape, twice);
-  if (nc0 <= 128) return launch_x12_T<N, 4>(f, out, g, ab1, s1, ab2, s2, st, shape, twice);
+  if (nc0 <= 64) return launch_x12_T<N, 2>(f, out, g, ab1, s1, ab2, s2, st, shape);
+  if (nc0 <= 128) return launch_x12_T<N, 4>(f, out, g, ab1, s1, ab2, s2, st, shape);
   return cudaErrorNotSupported;
 }
 

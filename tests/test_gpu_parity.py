@@ -471,33 +471,3 @@ def test_fused_drift_shifts_of_many_cells(lib, orc, deg, nc, dt, prec):
     ref = orc.sweep(og, 1, orc.sweep(og, 0, f, frac=0.5), frac=0.5).reshape(og.shape)
     assert relerr(get(s), ref) < (2 * TOL64 if prec == "fp64" else 2 * TOL32)
     s.close()
-
-
-@pytest.mark.parametrize("deg,nc", [(2, (64, 64, 3, 2)), (1, (16, 12, 7, 6)), (2, (13, 11, 4, 3))])
-def test_fp32_paired_drifts_are_the_separate_drifts(lib, orc, deg, nc):
-    # FP32: within one call the last half drift of a step and the first of
-    # the next run as one pass over each x-plane; the bits are those of
-    # single steps, and one x pass per step is saved
-    params = (0.5, 0.5, 0.5)
-    s, og = make(lib, orc, deg, nc, dt=0.05, prec="fp32")
-    s.set_initial(0, params)
-    s.timing(True)
-    W = s.step(4, history=True)
-    t = s.timing_read()
-    s.timing(False)
-    fused = t["x12"][1] > 0
-    if fused:
-        assert t["x12"][1] == 5  # D | K DD | K DD | K DD | K D
-    got = get(s)
-    W2 = s.step(3, history=True)  # replayed bodies (CUDA graph)
-    got2 = get(s)
-    s.close()
-    s1, _ = make(lib, orc, deg, nc, dt=0.05, prec="fp32")
-    s1.set_initial(0, params)
-    Ws = [s1.step(1, history=True)[0] for _ in range(4)]
-    assert np.array_equal(get(s1), got) and np.array_equal(np.array(Ws), W)
-    Ws = [s1.step(1, history=True)[0] for _ in range(3)]
-    assert np.array_equal(get(s1), got2) and np.array_equal(np.array(Ws), W2)
-    s1.close()
-    ref, Wr, _, _ = orc.step(og, orc.init(og, 0, params), 4)
-    assert relerr(got, ref.reshape(og.shape)) < 1e-5 and relerr(W, Wr) < 1e-5
