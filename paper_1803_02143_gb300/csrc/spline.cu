@@ -20,7 +20,10 @@
 // A CTA takes 32 lines (a 32-column tile of a strided direction, or 32
 // consecutive x1 lines) into shared memory as [n][33] (padded: the lines
 // are the columns), four threads per line (chunks of ceil(n/4) points).
+#include <algorithm>
+
 #include "ctx.h"
+#include "sweep_kernels.cuh"
 
 namespace sldg {
 
@@ -48,138 +51,177 @@ __global__ void k_spline_shifts(long long count, const double* __restrict__ src,
 // CONTIG: the lines are contiguous (x1); otherwise element i of line
 // (block b, column j) is at b n inner + i inner + j.  KEYCOL: the shift key
 // is the column (v-sweeps); otherwise the block (x-sweeps), key =
-// (block / key_div) % key_mod.
-template <typename T, bool CONTIG, bool KEYCOL>
+// (block / key_div) % key_mod.  A CTA walks tiles tile0, tile0 + gridDim.x,
+// ...: with NB = 2 the next tile is staged by cp.async into the second
+// input buffer while the current one is computed (NB = 1: lines too long
+// for three [n][33] buffers stage each tile after the previous one).
+template <typename T, bool CONTIG, bool KEYCOL, int NB>
 __global__ void __launch_bounds__(kSplThreads)
     k_spline_sweep(T* __restrict__ f, int n, long long inner, long long outer,
-                   long long tiles_per_block, const T* __restrict__ theta,
+                   long long tiles_per_block, long long ntiles, const T* __restrict__ theta,
                    const int* __restrict__ svec, long long key_div, long long key_mod, T z,
                    int W) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* U = reinterpret_cast<T*>(smraw);  // [n][kSplPitch]
-  T* Y = U + (size_t)n * kSplPitch;
+  T* Ubuf = reinterpret_cast<T*>(smraw);     // two input buffers [n][kSplPitch]
+  T* Y = Ubuf + NB * (size_t)n * kSplPitch;  // [n][kSplPitch]
   const int tid = threadIdx.x;
-  long long b0, j0;  // first line: block, column
-  int nl;            // lines of this tile
-  if (CONTIG) {
-    b0 = blockIdx.x * (long long)kSplLines;
-    j0 = 0;
-    nl = (int)min((long long)kSplLines, outer - b0);
-  } else {
-    b0 = blockIdx.x / tiles_per_block;
-    j0 = (blockIdx.x - b0 * tiles_per_block) * kSplLines;
-    nl = (int)min((long long)kSplLines, inner - j0);
-  }
-  T* base = CONTIG ? f + b0 * n : f + b0 * n * inner + j0;
-
-  // stage: every read coalesced (a warp along a line, or along a row of the
-  // column tile); the padded pitch keeps the transposed writes conflict-free
   const int warp = tid / kSplLines, lane = tid % kSplLines;
   constexpr int kWarps = kSplThreads / kSplLines;
-  if (CONTIG) {
-    for (int l = warp; l < nl; l += kWarps) {
-      const T* src = base + (long long)l * n;
-      for (int i = lane; i < n; i += kSplLines) U[i * kSplPitch + l] = src[i];
+  struct Tile {
+    long long b0, j0;  // first line: block, column
+    int nl;            // lines of this tile
+  };
+  auto tile_of = [&](long long t) {
+    Tile x;
+    if (CONTIG) {
+      x.b0 = t * kSplLines;
+      x.j0 = 0;
+      x.nl = (int)min((long long)kSplLines, outer - x.b0);
+    } else {
+      x.b0 = t / tiles_per_block;
+      x.j0 = (t - x.b0 * tiles_per_block) * kSplLines;
+      x.nl = (int)min((long long)kSplLines, inner - x.j0);
     }
-  } else if (lane < nl) {
-    for (int i = warp; i < n; i += kWarps) U[i * kSplPitch + lane] = base[(long long)i * inner + lane];
-  }
-  __syncthreads();
+    return x;
+  };
+  auto base_of = [&](const Tile& x) {
+    return CONTIG ? f + x.b0 * n : f + x.b0 * n * inner + x.j0;
+  };
+  // staging: every read coalesced (a warp along a line, or along a row of
+  // the column tile); the padded pitch keeps the transposed writes free of
+  // bank conflicts
+  auto stage = [&](const Tile& x, T* U) {
+    const T* base = base_of(x);
+    if (CONTIG) {
+      for (int l = warp; l < x.nl; l += kWarps) {
+        const T* src = base + (long long)l * n;
+        for (int i = lane; i < n; i += kSplLines)
+          cp_async_elem<sizeof(T)>(U + i * kSplPitch + l, src + i);
+      }
+    } else if (lane < x.nl) {
+      for (int i = warp; i < n; i += kWarps)
+        cp_async_elem<sizeof(T)>(U + i * kSplPitch + lane, base + (long long)i * inner + lane);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
 
   const int l = tid % kSplLines, c = tid / kSplLines;
   const int C = (n + kSplChunks - 1) / kSplChunks;
   const int ib = min(c * C, n), ie = min(ib + C, n);
-  const bool act = l < nl && ib < ie;
-  T* Ul = U + l;
-  T* Yl = Y + l;
-  // causal recurrence y_i = u_i - z y_{i-1}
-  if (act) {
-    T y = T(0);
-    int k = (ib - W) % n;
-    if (k < 0) k += n;
-    for (int t = 0; t < W; ++t) {
-      y = fma(-z, y, Ul[k * kSplPitch]);
+  long long t = blockIdx.x;
+  if (NB == 2 && t < ntiles) stage(tile_of(t), Ubuf);
+  for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+    const Tile x = tile_of(t);
+    T* U = Ubuf + (size_t)(NB == 2 ? b : 0) * n * kSplPitch;
+    if (NB == 1) stage(x, U);  // the previous tile's reads of U ended at its last barrier
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // this tile staged; the other buffer and Y are free
+    if (NB == 2 && t + gridDim.x < ntiles)
+      stage(tile_of(t + gridDim.x), Ubuf + (size_t)(b ^ 1) * n * kSplPitch);
+    const bool act = l < x.nl && ib < ie;
+    T* Ul = U + l;
+    T* Yl = Y + l;
+    // causal recurrence y_i = u_i - z y_{i-1}
+    if (act) {
+      T y = T(0);
+      int k = (ib - W) % n;
+      if (k < 0) k += n;
+      for (int q = 0; q < W; ++q) {
+        y = fma(-z, y, Ul[k * kSplPitch]);
+        k = k + 1 == n ? 0 : k + 1;
+      }
+      for (int i = ib; i < ie; ++i) {
+        y = fma(-z, y, Ul[i * kSplPitch]);
+        Yl[i * kSplPitch] = y;
+      }
+    }
+    __syncthreads();
+    // anti-causal recurrence v_i = y_i - z v_{i+1}; w = 6 z v over u
+    if (act) {
+      T v = T(0);
+      int k = (ie - 1 + W) % n;
+      for (int q = 0; q < W; ++q) {
+        v = fma(-z, v, Yl[k * kSplPitch]);
+        k = k == 0 ? n - 1 : k - 1;
+      }
+      const T sz = T(6) * z;
+      for (int i = ie - 1; i >= ib; --i) {
+        v = fma(-z, v, Yl[i * kSplPitch]);
+        Ul[i * kSplPitch] = sz * v;
+      }
+    }
+    __syncthreads();
+    // the interpolant at the shifted points
+    if (act) {
+      const long long key = KEYCOL ? (x.j0 + l) % key_mod
+                                   : ((CONTIG ? x.b0 + l : x.b0) / key_div) % key_mod;
+      const T th = theta[key];
+      const int s = svec[key];
+      const T om = T(1) - th, sixth = T(1) / T(6);
+      const T w0 = th * th * th * sixth;
+      const T w1 = (T(4) - T(6) * om * om + T(3) * om * om * om) * sixth;
+      const T w2 = (T(4) - T(6) * th * th + T(3) * th * th * th) * sixth;
+      const T w3 = om * om * om * sixth;
+      int k = (ib - s - 2) % n;
+      if (k < 0) k += n;
+      T c0 = Ul[k * kSplPitch];
       k = k + 1 == n ? 0 : k + 1;
-    }
-    for (int i = ib; i < ie; ++i) {
-      y = fma(-z, y, Ul[i * kSplPitch]);
-      Yl[i * kSplPitch] = y;
-    }
-  }
-  __syncthreads();
-  // anti-causal recurrence v_i = y_i - z v_{i+1}; w = 6 z v over u
-  if (act) {
-    T v = T(0);
-    int k = (ie - 1 + W) % n;
-    for (int t = 0; t < W; ++t) {
-      v = fma(-z, v, Yl[k * kSplPitch]);
-      k = k == 0 ? n - 1 : k - 1;
-    }
-    const T sz = T(6) * z;
-    for (int i = ie - 1; i >= ib; --i) {
-      v = fma(-z, v, Yl[i * kSplPitch]);
-      Ul[i * kSplPitch] = sz * v;
-    }
-  }
-  __syncthreads();
-  // the interpolant at the shifted points
-  if (act) {
-    const long long key = KEYCOL ? (j0 + l) % key_mod
-                                 : ((CONTIG ? b0 + l : b0) / key_div) % key_mod;
-    const T th = theta[key];
-    const int s = svec[key];
-    const T om = T(1) - th, sixth = T(1) / T(6);
-    const T w0 = th * th * th * sixth;
-    const T w1 = (T(4) - T(6) * om * om + T(3) * om * om * om) * sixth;
-    const T w2 = (T(4) - T(6) * th * th + T(3) * th * th * th) * sixth;
-    const T w3 = om * om * om * sixth;
-    int k = (ib - s - 2) % n;
-    if (k < 0) k += n;
-    T c0 = Ul[k * kSplPitch];
-    k = k + 1 == n ? 0 : k + 1;
-    T c1 = Ul[k * kSplPitch];
-    k = k + 1 == n ? 0 : k + 1;
-    T c2 = Ul[k * kSplPitch];
-    k = k + 1 == n ? 0 : k + 1;
-    for (int i = ib; i < ie; ++i) {
-      const T c3 = Ul[k * kSplPitch];
+      T c1 = Ul[k * kSplPitch];
       k = k + 1 == n ? 0 : k + 1;
-      Yl[i * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * c3)));
-      c0 = c1;
-      c1 = c2;
-      c2 = c3;
+      T c2 = Ul[k * kSplPitch];
+      k = k + 1 == n ? 0 : k + 1;
+      for (int i = ib; i < ie; ++i) {
+        const T c3 = Ul[k * kSplPitch];
+        k = k + 1 == n ? 0 : k + 1;
+        Yl[i * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * c3)));
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+      }
     }
-  }
-  __syncthreads();
-  if (CONTIG) {
-    for (int ll = warp; ll < nl; ll += kWarps) {
-      T* dst = base + (long long)ll * n;
-      for (int i = lane; i < n; i += kSplLines) dst[i] = Y[i * kSplPitch + ll];
+    __syncthreads();
+    T* base = base_of(x);
+    if (CONTIG) {
+      for (int ll = warp; ll < x.nl; ll += kWarps) {
+        T* dst = base + (long long)ll * n;
+        for (int i = lane; i < n; i += kSplLines) dst[i] = Y[i * kSplPitch + ll];
+      }
+    } else if (lane < x.nl) {
+      for (int i = warp; i < n; i += kWarps)
+        base[(long long)i * inner + lane] = Y[i * kSplPitch + lane];
     }
-  } else if (lane < nl) {
-    for (int i = warp; i < n; i += kWarps) base[(long long)i * inner + lane] = Y[i * kSplPitch + lane];
   }
 }
 
 template <typename T, bool CONTIG, bool KEYCOL>
 cudaError_t launch_spline_T(const SweepArgs& a, cudaStream_t st) {
   const int n = a.nc;
-  const size_t smem = 2 * (size_t)n * kSplPitch * sizeof(T);
-  if (n < 3 || smem > 227 * 1024) return cudaErrorNotSupported;
-  auto kfn = k_spline_sweep<T, CONTIG, KEYCOL>;
+  const size_t buf = (size_t)n * kSplPitch * sizeof(T);
+  if (n < 3 || 2 * buf > 227 * 1024) return cudaErrorNotSupported;
+  const int nb = 3 * buf <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
+  const size_t smem = (nb + 1) * buf;
+  auto kfn = nb == 2 ? k_spline_sweep<T, CONTIG, KEYCOL, 2> : k_spline_sweep<T, CONTIG, KEYCOL, 1>;
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long tiles_per_block = CONTIG ? 1 : (a.inner + kSplLines - 1) / kSplLines;
-  const long long blocks = CONTIG ? (a.outer + kSplLines - 1) / kSplLines : a.outer * tiles_per_block;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const long long ntiles = CONTIG ? (a.outer + kSplLines - 1) / kSplLines : a.outer * tiles_per_block;
+  // persistent CTAs: as many as are resident at once (by shared memory,
+  // at most 8 per SM), each walking tiles with a stride of the grid
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long per_sm = std::max<long long>(1, std::min<long long>(8, (228 * 1024) / (smem + 1024)));
+  const long long blocks = std::min<long long>(ntiles, per_sm * sms);
+  if (blocks < 1) return cudaSuccess;
   const T z = T(2.0 - 1.7320508075688772);  // 2 - sqrt(3)
   const int W = sizeof(T) == 8 ? 32 : 16;
   kfn<<<(unsigned)blocks, kSplThreads, smem, st>>>(
-      static_cast<T*>(a.f), n, a.inner, a.outer, tiles_per_block, static_cast<const T*>(a.ab),
-      a.s, a.key_div, a.key_mod, z, W);
+      static_cast<T*>(a.f), n, a.inner, a.outer, tiles_per_block, ntiles,
+      static_cast<const T*>(a.ab), a.s, a.key_div, a.key_mod, z, W);
   return cudaGetLastError();
 }
 

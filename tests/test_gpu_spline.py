@@ -47,7 +47,9 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("nc", [(37, 5, 9, 40), (8, 33, 70, 3)])
+# (300, 4, 3, 310): FP64 lines too long for two staged tiles of 300 points
+# (the single-buffer form); many tiles per CTA on the other grids
+@pytest.mark.parametrize("nc", [(37, 5, 9, 40), (8, 33, 70, 3), (300, 4, 3, 310)])
 @pytest.mark.parametrize("dim", [0, 1, 2, 3])
 def test_spline_sweep_matches_oracle(lib, orc, prec, nc, dim):
     s, og = _make(lib, orc, nc, 0.37, prec)
