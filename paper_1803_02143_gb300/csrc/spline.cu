@@ -121,16 +121,37 @@ __global__ void __launch_bounds__(kSplThreads)
     const bool act = l < x.nl && ib < ie;
     T* Ul = U + l;
     T* Yl = Y + l;
-    // causal recurrence y_i = u_i - z y_{i-1}
+    // The recurrences run eight points at a time: the eight shared-memory
+    // loads of a batch are issued before its chain of dependent FMAs.
+    constexpr int B8 = 8;
+    // causal recurrence y_i = u_i - z y_{i-1}: W warm-up points (a multiple
+    // of 8) from zero, then the chunk ib .. ie - 1 into Y
     if (act) {
       T y = T(0);
       int k = (ib - W) % n;
       if (k < 0) k += n;
-      for (int q = 0; q < W; ++q) {
-        y = fma(-z, y, Ul[k * kSplPitch]);
-        k = k + 1 == n ? 0 : k + 1;
+      for (int q0 = 0; q0 < W; q0 += B8) {
+        T u[B8];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          u[q] = Ul[k * kSplPitch];
+          k = k + 1 == n ? 0 : k + 1;
+        }
+#pragma unroll
+        for (int q = 0; q < B8; ++q) y = fma(-z, y, u[q]);
       }
-      for (int i = ib; i < ie; ++i) {
+      int i = ib;
+      for (; i + B8 <= ie; i += B8) {
+        T u[B8];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) u[q] = Ul[(i + q) * kSplPitch];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          y = fma(-z, y, u[q]);
+          Yl[(i + q) * kSplPitch] = y;
+        }
+      }
+      for (; i < ie; ++i) {
         y = fma(-z, y, Ul[i * kSplPitch]);
         Yl[i * kSplPitch] = y;
       }
@@ -140,12 +161,29 @@ __global__ void __launch_bounds__(kSplThreads)
     if (act) {
       T v = T(0);
       int k = (ie - 1 + W) % n;
-      for (int q = 0; q < W; ++q) {
-        v = fma(-z, v, Yl[k * kSplPitch]);
-        k = k == 0 ? n - 1 : k - 1;
+      for (int q0 = 0; q0 < W; q0 += B8) {
+        T u[B8];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          u[q] = Yl[k * kSplPitch];
+          k = k == 0 ? n - 1 : k - 1;
+        }
+#pragma unroll
+        for (int q = 0; q < B8; ++q) v = fma(-z, v, u[q]);
       }
       const T sz = T(6) * z;
-      for (int i = ie - 1; i >= ib; --i) {
+      int i = ie - 1;
+      for (; i - B8 + 1 >= ib; i -= B8) {
+        T u[B8];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) u[q] = Yl[(i - q) * kSplPitch];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          v = fma(-z, v, u[q]);
+          Ul[(i - q) * kSplPitch] = sz * v;
+        }
+      }
+      for (; i >= ib; --i) {
         v = fma(-z, v, Yl[i * kSplPitch]);
         Ul[i * kSplPitch] = sz * v;
       }
@@ -170,7 +208,23 @@ __global__ void __launch_bounds__(kSplThreads)
       k = k + 1 == n ? 0 : k + 1;
       T c2 = Ul[k * kSplPitch];
       k = k + 1 == n ? 0 : k + 1;
-      for (int i = ib; i < ie; ++i) {
+      int i = ib;
+      for (; i + B8 <= ie; i += B8) {
+        T u[B8];
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          u[q] = Ul[k * kSplPitch];
+          k = k + 1 == n ? 0 : k + 1;
+        }
+#pragma unroll
+        for (int q = 0; q < B8; ++q) {
+          Yl[(i + q) * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * u[q])));
+          c0 = c1;
+          c1 = c2;
+          c2 = u[q];
+        }
+      }
+      for (; i < ie; ++i) {
         const T c3 = Ul[k * kSplPitch];
         k = k + 1 == n ? 0 : k + 1;
         Yl[i * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * c3)));
