@@ -81,6 +81,8 @@ def parse():
                    help="workload the ncu report was captured on")
     p.add_argument("--ncu-targets", default=f"{DEFAULT_WORKLOAD},nonlinear_landau_64",
                    help="workloads (same degree and x-grid) the traffic is scaled to")
+    p.add_argument("--summarize-launches", default=None, metavar="CSV",
+                   help="print the per-kernel table of an ncu launch list (gpu__time_duration)")
     return p.parse_args()
 
 
@@ -246,6 +248,33 @@ def _kernel_kind(name):
         if periodic and not percol:
             return "x2", prec
     return None
+
+
+def summarize_launches(path):
+    """Launches, total device time and share per kernel of an ncu launch list
+    (--metrics gpu__time_duration.sum --csv), as a markdown table."""
+    import csv
+
+    with open(path) as fh:
+        rows = [r for r in csv.reader(fh) if len(r) > 5]
+    head = rows[0]
+    ci, cn, cu, cv = (head.index(k) for k in ("ID", "Kernel Name", "Metric Unit", "Metric Value"))
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0,
+             "msecond": 1.0, "s": 1e3, "second": 1e3}
+    tot, cnt = {}, {}
+    for r in rows[1:]:
+        if not r[ci].strip().isdigit():
+            continue
+        name = r[cn].split("(")[0].replace("void ", "").replace("sldg::", "").strip()
+        ms = float(r[cv].replace(",", "")) * scale.get(r[cu].strip().lower(), 1e-6)
+        tot[name] = tot.get(name, 0.0) + ms
+        cnt[name] = cnt.get(name, 0) + 1
+    allms = sum(tot.values())
+    print(f"{sum(cnt.values())} launches, {allms:.2f} ms of device time (serialised, cold caches)\n")
+    print("| kernel | launches | total ms | share |")
+    print("|---|---|---|---|")
+    for name in sorted(tot, key=lambda k: -tot[k]):
+        print(f"| `{name}` | {cnt[name]} | {tot[name]:.3f} | {100 * tot[name] / allms:.1f}% |")
 
 
 def ingest_ncu(args):
@@ -734,6 +763,9 @@ def main():
     args = parse()
     if args.ingest_ncu:
         ingest_ncu(args)
+        return
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
         return
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -5,15 +5,19 @@
 //   1. every CTA stages its rows (cp.async, contiguous in f);
 //   2. X1 in place on its rows, warp per row pair (each lane reads all the
 //      source cells of its outputs into registers before the warp writes);
-//   3. cluster barrier: every CTA's X1 rows are final;
-//   4. X2 for the CTA's own rows: the source rows of an output cell (a few
-//      rows away, periodic in x2) are read from this CTA's shared memory or,
-//      across the row split, from the owning CTA's through distributed
-//      shared memory; outputs go straight to f as float2 rows;
+//   3. the CTA signals its peers that its X1 rows are final (the first half
+//      of a split cluster barrier);
+//   4. X2 for the CTA's own rows: first the outputs whose source rows (a few
+//      rows away, periodic in x2) all lie in this CTA's shared memory, then,
+//      after waiting for the peers, those that read a row across the split
+//      from the owning CTA through distributed shared memory; outputs go
+//      straight to f as float2 rows;
 //   5. cluster barrier: no CTA leaves while a peer may still read its rows.
 // f is read once and written once for both sweeps.  The arithmetic of every
 // output is that of the separate packed kernels (sweep_f32x2.cuh).
 #pragma once
+
+#include <algorithm>
 
 #include "sweep_f32x2.cuh"
 
@@ -64,7 +68,7 @@ __host__ __device__ __forceinline__ int x12_lanes_per_pair(int nc0, int cpl) {
 // groups per warp in the X1 phase (lines of at most 16 CPL cells)
 template <int N, int CPL, bool GRP>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
-    k_sweep_x12_f32(const float* src, float* dst, int nc0, int nc1, int cs, int D2, int D3,
+    k_sweep_x12_f32(const float* src, float* dst, int nc0, int nc1, int cs, int run, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
                     const float* __restrict__ ab2, const int* __restrict__ s2) {
   constexpr int NN = N * N;
@@ -136,10 +140,15 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       __syncwarp(gmask);
     }
   }
-  // 3. every CTA's rows hold X1 f
-  cluster_sync();
+  // 3. this CTA's X1 rows are final for all of its warps; its peers may read
+  //    them from now on
+  __syncthreads();
+  cluster_arrive();
 
-  // 4. X2 for rows rank*H .. rank*H + H - 1
+  // 4. X2 for rows rank*H .. rank*H + H - 1: first the runs of cells whose
+  //    source rows all lie in this CTA, then (after the peers' X1) the runs
+  //    that read a peer's rows through distributed shared memory; outputs
+  //    go straight to f as float2 rows
   {
     float2 A[NN], B[NN];
 #pragma unroll
@@ -148,43 +157,72 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
       A[i] = make_float2(a, a);
       B[i] = make_float2(b, b);
     }
-    const int sa = wrap_cell(-s2[key2] - 1, nc1);
+    const int d = -s2[key2] - 1;  // sources of output cell c: c + d, c + d + 1
+    const int sa = wrap_cell(d, nc1);
     const int npairs = D0 / 2;
-    const int items = npairs * kX12Groups;
-    auto load = [&](int kcell, int c0, float2* xv) {
-      const int owner = kcell / cells_per;
-      const int lrow = (kcell - owner * cells_per) * N;
-      if (owner == (int)rank) {
+    const int items = npairs * ((cells_per + run - 1) / run);
+    // exact quotients of small operands (< 2^16) by a 32-bit reciprocal
+    const unsigned inv_np = 0xFFFFFFFFu / (unsigned)npairs + 1u;
+    const unsigned inv_cp = 0xFFFFFFFFu / (unsigned)cells_per + 1u;
+    auto local_load = [&](int lcell, int c0, float2* xv) {
 #pragma unroll
-        for (int l = 0; l < N; ++l)
-          xv[l] = *reinterpret_cast<const float2*>(rows + (lrow + l) * D0 + c0);
+      for (int l = 0; l < N; ++l)
+        xv[l] = *reinterpret_cast<const float2*>(rows + (lcell * N + l) * D0 + c0);
+    };
+    auto any_load = [&](int owner, int lcell, int c0, float2* xv) {
+      if (owner == (int)rank) {
+        local_load(lcell, c0, xv);
       } else {
-        const unsigned base = cluster_map(rows + lrow * D0 + c0, (unsigned)owner);
+        const unsigned base = cluster_map(rows + lcell * N * D0 + c0, (unsigned)owner);
 #pragma unroll
         for (int l = 0; l < N; ++l) xv[l] = ld_cluster_f2(base + (unsigned)(l * D0 * 4));
       }
     };
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int q = it % npairs, g = it / npairs;
-      const int c0 = 2 * q;
-      const int lb = (g * cells_per) / kX12Groups, le = ((g + 1) * cells_per) / kX12Groups;
-      if (lb >= le) continue;
-      const int cglob = (int)rank * cells_per + lb;
-      int k = cglob + sa;
-      if (k >= nc1) k -= nc1;
-      float2 xa[N], xb[N];
-      load(k, c0, xa);
-      float* out = op + (long long)(cglob * N) * D0 + c0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) cluster_wait();  // every peer's X1 rows are final
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int g = (int)__umulhi((unsigned)it, inv_np);
+        const int c0 = 2 * (it - g * npairs);
+        const int lb = g * run, le = min(lb + run, cells_per);
+        const bool local = lb + d >= 0 && le + d <= cells_per - 1;
+        if (local != (pass == 0)) continue;
+        const int cglob = (int)rank * cells_per + lb;
+        float2 xa[N], xb[N];
+        float* out = op + (long long)(cglob * N) * D0 + c0;
+        if (local) {
+          int k = lb + d;
+          local_load(k, c0, xa);
 #pragma unroll 1
-      for (int c = lb; c < le; ++c, out += N * D0) {
-        k = k + 1 == nc1 ? 0 : k + 1;
-        load(k, c0, xb);
-        float2 y[N];
-        f2_cell<N>(A, B, xa, xb, y);
+          for (int c = lb; c < le; ++c, out += N * D0) {
+            local_load(++k, c0, xb);
+            float2 y[N];
+            f2_cell<N>(A, B, xa, xb, y);
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2*>(out + j * D0) = y[j];
+            for (int j = 0; j < N; ++j) *reinterpret_cast<float2*>(out + j * D0) = y[j];
 #pragma unroll
-        for (int l = 0; l < N; ++l) xa[l] = xb[l];
+            for (int l = 0; l < N; ++l) xa[l] = xb[l];
+          }
+        } else {
+          int k = cglob + sa;
+          if (k >= nc1) k -= nc1;
+          int owner = (int)__umulhi((unsigned)k, inv_cp);
+          int lk = k - owner * cells_per;
+          any_load(owner, lk, c0, xa);
+#pragma unroll 1
+          for (int c = lb; c < le; ++c, out += N * D0) {
+            if (++lk == cells_per) {
+              lk = 0;
+              owner = owner + 1 == cs ? 0 : owner + 1;
+            }
+            any_load(owner, lk, c0, xb);
+            float2 y[N];
+            f2_cell<N>(A, B, xa, xb, y);
+#pragma unroll
+            for (int j = 0; j < N; ++j) *reinterpret_cast<float2*>(out + j * D0) = y[j];
+#pragma unroll
+            for (int l = 0; l < N; ++l) xa[l] = xb[l];
+          }
+        }
       }
     }
   }
@@ -216,6 +254,8 @@ cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* 
   }
   if (cs == 0 || planes * cs > 0x7fffffffLL) return cudaErrorNotSupported;
   const size_t smem = (size_t)(nc1 / cs) * N * D0 * sizeof(float);
+  const int cells_per = nc1 / cs;
+  const int run = std::max(1, (cells_per + kX12Groups - 1) / kX12Groups);  // cells per X2 item
   auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_f32<N, CPL, true>
                                                : k_sweep_x12_f32<N, CPL, false>;
   cudaError_t e = set_smem(kfn, smem);
@@ -236,7 +276,7 @@ cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* 
     shape[0] = cs;
     shape[1] = x12_lanes_per_pair(nc0, CPL);
   }
-  return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, (int)g.D[2], (int)g.D[3],
+  return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
                             static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2);
 }
 
