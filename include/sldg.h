@@ -196,7 +196,10 @@ int sldg_set_f(sldg_ctx* ctx, const void* src, int on_device, double t, long lon
  * compositions those flags describe.  If W_history (host, nsteps doubles)
  * is non-NULL it receives the electric energy W(E) of each step's (first)
  * kick field and the call synchronises the stream; otherwise the call is
- * asynchronous.
+ * asynchronous.  FP64 storage with double-float sweeps: f holds IEEE doubles
+ * before and after the call; between the steps of one call the state stays
+ * in the sweeps' double-float pairs, so one call of n steps and n calls of
+ * one step agree to rounding (about 2^-47 relative per step), not bit for bit.
  * Errors: ARG (nsteps < 0), CUDA. */
 int sldg_step(sldg_ctx* ctx, int nsteps, double* W_history);
 

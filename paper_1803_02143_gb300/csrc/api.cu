@@ -169,7 +169,7 @@ void free_all(sldg_ctx* c) {
   dfree(c->d_ckpool); dfree(c->d_seg); dfree(c->d_Ecap);
   for (int i = 0; i < 4; ++i) dfree(c->d_work[i]);
   dfree(c->d_alt);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
     c->step_graph[i] = nullptr;
   }
@@ -231,7 +231,7 @@ bool df_states(const sldg_ctx* c) {
 }
 
 void drop_step_graphs(sldg_ctx* c) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
     c->step_graph[i] = nullptr;
   }
@@ -656,10 +656,12 @@ int forward_stage(sldg_ctx* c, const void* src, void* g2_out, void* g3_out, doub
 // The repeated unit of sldg_step: a whole step (IEEE in and out), or with
 // merged drifts the body of a step that another step follows (double-float
 // pairs in and out on FP64 storage).
-int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter) {
+int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter, bool chained) {
   int wi = 0;
   if (merged(c)) return run_stages(c, buf, merged_body(c, false), false, false, Wslot, Wcounter, &wi);
-  return run_stages(c, buf, step_stages(c), true, true, Wslot, Wcounter, &wi);
+  // chained: a step between two steps of the same call, whose state stays
+  // in double-float pairs on FP64 storage
+  return run_stages(c, buf, step_stages(c), !chained, !chained, Wslot, Wcounter, &wi);
 }
 
 // nsteps units of f as replays of one recorded unit (a CUDA graph), W of
@@ -667,8 +669,10 @@ int run_unit(sldg_ctx* c, void* buf, double* Wslot, int* Wcounter) {
 // reset_counter).  *replayed stays false when graphs do not apply (fewer
 // than two units, per-kernel timing on, or an earlier capture failed) and
 // the caller runs the units eagerly.
-int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed) {
+int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, bool* replayed,
+                 bool chained = false) {
   const int hv = Wbase ? 1 : 0;
+  const int k = hv + (chained ? 2 : 0);  // graph slot: unit kind, W history or not
   *replayed = false;
   if (nsteps >= 2 && !c->timing && !c->graphs_off) {
     // one recorded step replayed nsteps times: the launch overhead of the
@@ -677,37 +681,37 @@ int replay_steps(sldg_ctx* c, int nsteps, double* Wbase, bool reset_counter, boo
     SLDG_TRY(prepare_xmats(c));
     for (int d = 0; d < 2; ++d) SLDG_TRY(alloc_matset(c, &c->vm[d], c->g.Dx, false, false));
     if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
-    if (c->step_graph[hv] && (c->step_graph_buf[hv] != c->f || c->step_graph_W[hv] != Wbase)) {
-      cudaGraphExecDestroy(c->step_graph[hv]);
-      c->step_graph[hv] = nullptr;
+    if (c->step_graph[k] && (c->step_graph_buf[k] != c->f || c->step_graph_W[k] != Wbase)) {
+      cudaGraphExecDestroy(c->step_graph[k]);
+      c->step_graph[k] = nullptr;
     }
-    if (!c->step_graph[hv]) {
+    if (!c->step_graph[k]) {
       const long long l0 = c->launches;
       cudaGraph_t graph = nullptr;
       bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      const int rc = ok ? run_unit(c, c->f, Wbase, hv ? c->d_counter : nullptr) : SLDG_ERR_CUDA;
+      const int rc = ok ? run_unit(c, c->f, Wbase, hv ? c->d_counter : nullptr, chained) : SLDG_ERR_CUDA;
       if (ok) ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && rc == SLDG_OK;
-      if (ok) ok = cudaGraphInstantiate(&c->step_graph[hv], graph, 0) == cudaSuccess;
+      if (ok) ok = cudaGraphInstantiate(&c->step_graph[k], graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
-      c->step_graph_launches[hv] = c->launches - l0;
+      c->step_graph_launches[k] = c->launches - l0;
       c->launches = l0;
       if (!ok) {
         cudaGetLastError();
-        if (c->step_graph[hv]) cudaGraphExecDestroy(c->step_graph[hv]);
-        c->step_graph[hv] = nullptr;
+        if (c->step_graph[k]) cudaGraphExecDestroy(c->step_graph[k]);
+        c->step_graph[k] = nullptr;
         c->graphs_off = true;
         invalidate_vmats(c);
         c->have_field = false;
       } else {
-        c->step_graph_buf[hv] = c->f;
-        c->step_graph_W[hv] = Wbase;
+        c->step_graph_buf[k] = c->f;
+        c->step_graph_W[k] = Wbase;
       }
     }
-    if (c->step_graph[hv]) {
+    if (c->step_graph[k]) {
       if (hv && reset_counter) SLDG_CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
       for (int m = 0; m < nsteps; ++m) {
-        SLDG_CU(cudaGraphLaunch(c->step_graph[hv], c->stream));
-        c->launches += c->step_graph_launches[hv];
+        SLDG_CU(cudaGraphLaunch(c->step_graph[k], c->stream));
+        c->launches += c->step_graph_launches[k];
         c->t += c->g.dt;
         c->step += 1;
       }
@@ -975,23 +979,42 @@ int sldg_step(sldg_ctx* c, int nsteps, double* W_history) {
   if (nsteps < 0) return SLDG_ERR_ARG;
   if (W_history) SLDG_TRY(ensure_W(c, nsteps));
   double* Wd = W_history ? c->d_W : nullptr;
-  // merged drifts: D(w_0/2), nsteps - 1 bodies (replayed), the last body
+  // merged drifts: D(w_0/2), nsteps - 1 bodies (replayed), the last body.
+  // Double-float sweeps on FP64 storage: the first step takes IEEE doubles
+  // and leaves double-float pairs, the steps between keep the pairs
+  // (replayed), the last one writes IEEE doubles again, so the state is
+  // converted once per call instead of twice per step.
   const bool mg = merged(c) && nsteps > 0;
-  const int units = mg ? nsteps - 1 : nsteps;
+  const bool dc = !mg && df_states(c) && nsteps >= 2;
+  const int units = mg ? nsteps - 1 : (dc ? nsteps - 2 : nsteps);
   if (mg) {
     double w[3];
     strang_weights(c, w);
     int wi = 0;
     SLDG_TRY(run_stages(c, c->f, {{false, false, 0.5 * w[0]}}, true, false, nullptr, nullptr, &wi));
   }
+  if (dc) {
+    int wi = 0;
+    SLDG_TRY(run_stages(c, c->f, step_stages(c), true, false, Wd, nullptr, &wi));
+    c->t += c->g.dt;
+    c->step += 1;
+  }
+  double* Wu = Wd && dc ? Wd + 1 : Wd;  // W slots of the replayed units
   bool replayed = false;
-  SLDG_TRY(replay_steps(c, units, Wd, true, &replayed));
+  SLDG_TRY(replay_steps(c, units, Wu, true, &replayed, dc));
   if (!replayed)
     for (int m = 0; m < units; ++m) {
-      SLDG_TRY(run_unit(c, c->f, Wd ? Wd + m : nullptr, nullptr));
+      SLDG_TRY(run_unit(c, c->f, Wu ? Wu + m : nullptr, nullptr, dc));
       c->t += c->g.dt;
       c->step += 1;
     }
+  if (dc) {
+    int wi = 0;
+    SLDG_TRY(run_stages(c, c->f, step_stages(c), false, true, Wd ? Wd + nsteps - 1 : nullptr,
+                        nullptr, &wi));
+    c->t += c->g.dt;
+    c->step += 1;
+  }
   if (mg) {
     int wi = 0;
     SLDG_TRY(run_stages(c, c->f, merged_body(c, true), false, true, Wd ? Wd + units : nullptr,

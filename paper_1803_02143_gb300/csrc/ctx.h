@@ -181,10 +181,11 @@ struct sldg_ctx {
   // sldg_step as a replayed CUDA graph of one step (two variants: without /
   // with the W history, whose slot comes from a device counter); with merged
   // drifts the graph holds the part of a step between two merged drifts
-  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
-  const void* step_graph_buf[2] = {nullptr, nullptr};  // f and W history they were made for
-  const void* step_graph_W[2] = {nullptr, nullptr};
-  long long step_graph_launches[2] = {0, 0};
+  // [W history or not + 2 * chained unit (a step between two steps of one call)]
+  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  const void* step_graph_buf[4] = {nullptr, nullptr, nullptr, nullptr};  // f and W history they were made for
+  const void* step_graph_W[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long step_graph_launches[4] = {0, 0, 0, 0};
   bool graphs_off = false;  // a capture failed: steps run eagerly from then on
   int* d_counter = nullptr;
 
