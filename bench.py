@@ -171,9 +171,14 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+HOST_HEADERS = ("ctx.h", "fields.cuh")  # the host context and launcher declarations
+
+
 def unit_sha1(unit):
     """SHA-1 of one kernel translation unit of csrc/ and every csrc/ header it
-    includes (recursively): the sources of the kernels it instantiates."""
+    includes (recursively): the sources of the kernels it instantiates.  The
+    host-only headers (the context structure, launcher declarations) are
+    followed for their includes but not hashed: they hold no device code."""
     d = os.path.join(ROOT, "paper_1803_02143_gb300", "csrc")
     seen = []
 
@@ -188,7 +193,7 @@ def unit_sha1(unit):
 
     visit(unit)
     h = hashlib.sha1()
-    for name in sorted(seen):
+    for name in sorted(n for n in seen if n not in HOST_HEADERS):
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())

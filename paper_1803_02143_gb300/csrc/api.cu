@@ -1203,18 +1203,36 @@ int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
     char* dst = reinterpret_cast<char*>(c->d_ckpool) + (size_t)(m0 / ckpt_every) * fb;
     SLDG_CU(cudaMemcpyAsync(dst, c->f, fb, cudaMemcpyDeviceToDevice, c->stream));
     const int ns = std::min(ckpt_every, nsteps - m0);
+    // double-float sweeps: the state stays in double-float pairs between the
+    // steps of a segment (IEEE at its ends, where the checkpoints are taken)
+    const bool dc = df_states(c) && ns >= 2;
+    int a = m0, b = m0 + ns;  // steps run as whole units
+    if (dc) {
+      int wi = 0;
+      SLDG_TRY(run_stages(c, c->f, step_stages(c), true, false, c->d_Wrec + m0, nullptr, &wi));
+      c->t += c->g.dt;
+      c->step += 1;
+      ++a;
+      --b;
+    }
     bool replayed = false;
-    if (ns >= 2 && !c->timing && !c->graphs_off) {
+    if (b - a >= 2 && !c->timing && !c->graphs_off) {
       if (!c->d_counter) SLDG_TRY(dalloc(&c->d_counter, sizeof(int)));
-      SLDG_CU(launch_set_int(c->d_counter, m0, c->stream));  // W of step m0 + i to d_Wrec[m0 + i]
-      SLDG_TRY(replay_steps(c, ns, c->d_Wrec, false, &replayed));
+      SLDG_CU(launch_set_int(c->d_counter, a, c->stream));  // W of step a + i to d_Wrec[a + i]
+      SLDG_TRY(replay_steps(c, b - a, c->d_Wrec, false, &replayed, dc));
     }
     if (!replayed)
-      for (int m = m0; m < m0 + ns; ++m) {
-        SLDG_TRY(do_step(c, c->f, c->d_Wrec + m));
+      for (int m = a; m < b; ++m) {
+        SLDG_TRY(run_unit(c, c->f, c->d_Wrec + m, nullptr, dc));
         c->t += c->g.dt;
         c->step += 1;
       }
+    if (dc) {
+      int wi = 0;
+      SLDG_TRY(run_stages(c, c->f, step_stages(c), false, true, c->d_Wrec + b, nullptr, &wi));
+      c->t += c->g.dt;
+      c->step += 1;
+    }
   }
   if (W_history) {
     SLDG_CU(cudaMemcpyAsync(W_history, c->d_Wrec, nsteps * sizeof(double), cudaMemcpyDeviceToHost,
