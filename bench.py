@@ -231,7 +231,7 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
 KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
                 ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),
                 ("k_sweep_strided_f2", "sweep_f32.cu"), ("k_sweep_x1_f2warp", "sweep_f32.cu"),
-                ("k_rho_partial", "fields.cu"))
+                ("k_rho_partial", "fields.cu"), ("k_spline_sweep", "spline.cu"))
 
 
 def _kernel_kind(name):
@@ -244,6 +244,11 @@ def _kernel_kind(name):
         return "x1", prec
     if "k_rho_partial" in name:
         return "rho", prec
+    m = re.search(r"k_spline_sweep<\s*\w+,\s*(\w+),\s*(\w+)", name)
+    if m:  # <T, CONTIG, KEYCOL, NB>: x1 lines contiguous, v-sweeps keyed by column
+        if m.group(1) in ("1", "true"):
+            return "x1", prec
+        return ("v", prec) if m.group(2) in ("1", "true") else ("x2", prec)
     m = re.search(r"k_sweep_strided_\w+<\s*\d+,\s*(\w+),\s*(\w+)", name)
     if m:
         periodic = m.group(1) in ("1", "true")
