@@ -626,20 +626,23 @@ int prepare_xmats(sldg_ctx* c) {
   return SLDG_OK;
 }
 
-// Step m of the forward again from its state src (IEEE doubles on FP64
-// storage; not modified), keeping what the adjoint of the step needs: g2
+// Step m of the forward again from its state src (not modified; IEEE
+// doubles, or double-float pairs when src_df: the states between the steps
+// of a recorded segment), keeping what the adjoint of the step needs: g2
 // (the input of V1, after the x half drifts) and g3 (the input of V2, after
 // V1) in the format of the step's intermediate states (double-float pairs
 // when the sweeps run in double-float arithmetic), and the kick field
 // (E_out, 2 D_0 D_1 doubles, nullable; the context's field holds it as
 // well).  Every sweep writes out of place into the next buffer, so nothing
 // is copied, and the states are those of do_step bit for bit (the same
-// kernels, arithmetic and formats).  full: finish the step into dst (which
-// may be src; its previous contents are overwritten).
+// kernels, arithmetic and formats as the recording, which keeps double-float
+// pairs between the steps of a segment).  full: finish the step into dst
+// (which may be src; its previous contents are overwritten), as double-float
+// pairs on FP64 storage with double-float sweeps.
 int forward_stage(sldg_ctx* c, const void* src, void* g2_out, void* g3_out, double* E_out,
-                  bool full, void* dst) {
+                  bool full, void* dst, bool src_df) {
   const bool df = df_states(c);
-  SLDG_TRY(drift(c, const_cast<void*>(src), 0.5, false, df, g2_out));
+  SLDG_TRY(drift(c, const_cast<void*>(src), 0.5, df && src_df, df, g2_out));
   SLDG_TRY(compute_fields(c, g2_out, df));
   if (E_out) {
     SLDG_CU(cudaMemcpyAsync(E_out, c->d_E[0], c->g.Dx * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -650,7 +653,7 @@ int forward_stage(sldg_ctx* c, const void* src, void* g2_out, void* g3_out, doub
   SLDG_TRY(run_sweep(c, g2_out, 2, 1.0, false, nullptr, nullptr, df, df, g3_out));
   if (!full) return SLDG_OK;
   SLDG_TRY(run_sweep(c, g3_out, 3, 1.0, false, nullptr, nullptr, df, df, dst));
-  return drift(c, dst, 0.5, df, false);
+  return drift(c, dst, 0.5, df, df);
 }
 
 // The repeated unit of sldg_step: a whole step (IEEE in and out), or with
@@ -1317,18 +1320,24 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
 
 // The same from the step's initial state fm (recomputing g2, g3 and the
 // field in the two work buffers)
-int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad) {
+int adjoint_step(sldg_ctx* c, const void* fm, int m, const double* cW, void* grad, bool fm_df) {
   void* g2 = c->d_work[0];
   void* g3 = c->d_work[1];
-  SLDG_TRY(forward_stage(c, fm, g2, g3, nullptr, false, nullptr));
+  SLDG_TRY(forward_stage(c, fm, g2, g3, nullptr, false, nullptr, fm_df));
   return adjoint_step_from(c, g2, g3, nullptr, m, cW, grad);
 }
 
 // dst <- src advanced by k Strang steps
-int advance(sldg_ctx* c, void* dst, const void* src, int k) {
+// dst <- src advanced by k >= 1 Strang steps inside a recorded segment: src
+// in IEEE doubles or (src_df) double-float pairs, dst as double-float pairs
+// on FP64 storage with double-float sweeps (the recording's states there)
+int advance(sldg_ctx* c, void* dst, const void* src, int k, bool src_df) {
   const size_t fb = c->g.N * c->esize;
   if (dst != src) SLDG_CU(cudaMemcpyAsync(dst, src, fb, cudaMemcpyDeviceToDevice, c->stream));
-  for (int i = 0; i < k; ++i) SLDG_TRY(do_step(c, dst, nullptr));
+  for (int i = 0; i < k; ++i) {
+    int wi = 0;
+    SLDG_TRY(run_stages(c, dst, step_stages(c), i == 0 && !src_df, false, nullptr, nullptr, &wi));
+  }
   c->bwd_recomputed += k;
   return SLDG_OK;
 }
@@ -1341,10 +1350,10 @@ int advance(sldg_ctx* c, void* dst, const void* src, int k) {
 // src.  Recomputation: none beyond one pass when b - a - 1 <= slots, about
 // log2(b - a) passes when slots run out.
 int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>& free,
-                  const double* cW, void* grad) {
+                  const double* cW, void* grad, bool src_df) {
   const size_t fb = c->g.N * c->esize;
   const int n = b - a;
-  if (n == 1) return adjoint_step(c, src, a, cW, grad);
+  if (n == 1) return adjoint_step(c, src, a, cW, grad, src_df);
   if ((size_t)(2 * n + 1) <= free.size() && c->d_Ecap && n <= c->Ecap_steps) {
     // one forward pass over the range keeps every step's g2, g3 and field
     std::vector<char*> st(free.end() - (2 * n + 1), free.end());
@@ -1353,7 +1362,7 @@ int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>
     const long long e2 = 2 * c->g.Dx;
     for (int i = 0; i < n; ++i) {
       SLDG_TRY(forward_stage(c, i == 0 ? src : w, st[2 * i], st[2 * i + 1], c->d_Ecap + i * e2,
-                             i + 1 < n, w));
+                             i + 1 < n, w, i == 0 ? src_df : true));
       if (i + 1 < n) c->bwd_recomputed += 1;
     }
     for (int m = b - 1; m >= a; --m)
@@ -1367,30 +1376,30 @@ int adjoint_range(sldg_ctx* c, const void* src, int a, int b, std::vector<char*>
     free.resize(free.size() - (n - 1));
     const void* prev = src;
     for (int i = 0; i < n - 1; ++i) {
-      SLDG_TRY(advance(c, st[i], prev, 1));
+      SLDG_TRY(advance(c, st[i], prev, 1, i == 0 ? src_df : true));
       prev = st[i];
     }
-    for (int m = b - 1; m > a; --m) SLDG_TRY(adjoint_step(c, st[m - a - 1], m, cW, grad));
-    SLDG_TRY(adjoint_step(c, src, a, cW, grad));
+    for (int m = b - 1; m > a; --m) SLDG_TRY(adjoint_step(c, st[m - a - 1], m, cW, grad, true));
+    SLDG_TRY(adjoint_step(c, src, a, cW, grad, src_df));
     free.insert(free.end(), st.begin(), st.end());
     return SLDG_OK;
   }
   if (free.size() == 1) {  // one slot: recompute every state from src
     char* w = free.back();
     for (int m = b - 1; m > a; --m) {
-      SLDG_TRY(advance(c, w, src, m - a));
-      SLDG_TRY(adjoint_step(c, w, m, cW, grad));
+      SLDG_TRY(advance(c, w, src, m - a, src_df));
+      SLDG_TRY(adjoint_step(c, w, m, cW, grad, true));
     }
-    return adjoint_step(c, src, a, cW, grad);
+    return adjoint_step(c, src, a, cW, grad, src_df);
   }
   const int mid = a + n / 2;
   char* s = free.back();
   free.pop_back();
-  SLDG_TRY(advance(c, s, src, mid - a));
-  SLDG_TRY(adjoint_range(c, s, mid, b, free, cW, grad));
+  SLDG_TRY(advance(c, s, src, mid - a, src_df));
+  SLDG_TRY(adjoint_range(c, s, mid, b, free, cW, grad, true));
   free.push_back(s);
   (void)fb;
-  return adjoint_range(c, src, a, mid, free, cW, grad);
+  return adjoint_range(c, src, a, mid, free, cW, grad, src_df);
 }
 
 }  // namespace
@@ -1468,7 +1477,7 @@ int sldg_backward(sldg_ctx* c, const double* cW, int ncW, void* grad, double* J_
   const int nseg = (int)c->ck_count;
   for (int sidx = nseg - 1; sidx >= 0; --sidx) {
     const int m0 = sidx * ck, m1 = std::min(m0 + ck, n);
-    SLDG_TRY(adjoint_range(c, pool + (size_t)sidx * fb, m0, m1, free, cW, grad));
+    SLDG_TRY(adjoint_range(c, pool + (size_t)sidx * fb, m0, m1, free, cW, grad, false));
   }
   // the context's field now belongs to the first step; leave f as recorded
   c->have_field = false;
