@@ -23,22 +23,31 @@ struct Basis {
   double inv_den[kMaxNodes];
 };
 
-// Lagrange basis polynomial phi_j(t) on the Gauss-Legendre nodes.
+// Lagrange basis polynomial phi_j(t) on the Gauss-Legendre nodes.  NT > 0:
+// the node count as a compile-time constant (NT = b.n; the loops unroll and
+// the operations are the same); NT = 0: b.n at run time.
+template <int NT = 0>
 __host__ __device__ inline double lagrange(const Basis& b, int j, double t) {
+  const int n = NT > 0 ? NT : b.n;
   double p = b.inv_den[j];
-  for (int m = 0; m < b.n; ++m)
-    if (m != j) p *= (t - b.xi[m]);
+#pragma unroll
+  for (int m = 0; m < (NT > 0 ? NT : kMaxNodes); ++m)
+    if (m < n && m != j) p *= (t - b.xi[m]);
   return p;
 }
 
 // phi_j'(t) = inv_den_j * sum_k prod_{m != j, k} (t - xi_m)
+template <int NT = 0>
 __host__ __device__ inline double lagrange_d(const Basis& b, int j, double t) {
+  const int n = NT > 0 ? NT : b.n;
   double s = 0.0;
-  for (int k = 0; k < b.n; ++k) {
-    if (k == j) continue;
+#pragma unroll
+  for (int k = 0; k < (NT > 0 ? NT : kMaxNodes); ++k) {
+    if (k >= n || k == j) continue;
     double p = 1.0;
-    for (int m = 0; m < b.n; ++m)
-      if (m != j && m != k) p *= (t - b.xi[m]);
+#pragma unroll
+    for (int m = 0; m < (NT > 0 ? NT : kMaxNodes); ++m)
+      if (m < n && m != j && m != k) p *= (t - b.xi[m]);
     s += p;
   }
   return s * b.inv_den[j];
@@ -52,31 +61,39 @@ __host__ __device__ inline double lagrange_d(const Basis& b, int j, double t) {
 //   B_jl = (1/w_j) int_theta^1 phi_j(t) phi_l(t - theta) dt,
 // integrated exactly by n-point Gauss-Legendre on each sub-interval (the
 // integrand has degree 2(n-1)).  dA, dB (nullable) are the theta
-// derivatives (Leibniz rule).  Row-major j*n + l.
+// derivatives (Leibniz rule).  Row-major j*n + l.  NT as for lagrange.
+template <int NT = 0>
 __host__ __device__ inline void build_ab(const Basis& b, double theta, double* A, double* B,
                                          double* dA, double* dB) {
-  const int n = b.n;
+  const int n = NT > 0 ? NT : b.n;
+  constexpr int U = NT > 0 ? NT : kMaxNodes;  // loop bound the compiler unrolls
   const double om = 1.0 - theta;
-  for (int j = 0; j < n; ++j) {
-    for (int l = 0; l < n; ++l) {
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    if (j >= n) break;
+#pragma unroll
+    for (int l = 0; l < U; ++l) {
+      if (l >= n) break;
       double a = 0.0, bb = 0.0, da = 0.0, db = 0.0;
-      for (int q = 0; q < n; ++q) {
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (q >= n) break;
         const double ta = theta * b.xi[q];
         const double tb = theta + om * b.xi[q];
-        const double pa = lagrange(b, j, ta), pb = lagrange(b, j, tb);
-        a += b.w[q] * pa * lagrange(b, l, ta + om);
-        bb += b.w[q] * pb * lagrange(b, l, tb - theta);
+        const double pa = lagrange<NT>(b, j, ta), pb = lagrange<NT>(b, j, tb);
+        a += b.w[q] * pa * lagrange<NT>(b, l, ta + om);
+        bb += b.w[q] * pb * lagrange<NT>(b, l, tb - theta);
         if (dA) {
-          da += b.w[q] * pa * lagrange_d(b, l, ta + om);
-          db += b.w[q] * pb * lagrange_d(b, l, tb - theta);
+          da += b.w[q] * pa * lagrange_d<NT>(b, l, ta + om);
+          db += b.w[q] * pb * lagrange_d<NT>(b, l, tb - theta);
         }
       }
       A[j * n + l] = theta * a / b.w[j];
       B[j * n + l] = om * bb / b.w[j];
       if (dA) {
-        const double pj = lagrange(b, j, theta);
-        dA[j * n + l] = (pj * lagrange(b, l, 1.0) - theta * da) / b.w[j];
-        dB[j * n + l] = (-pj * lagrange(b, l, 0.0) - om * db) / b.w[j];
+        const double pj = lagrange<NT>(b, j, theta);
+        dA[j * n + l] = (pj * lagrange<NT>(b, l, 1.0) - theta * da) / b.w[j];
+        dB[j * n + l] = (-pj * lagrange<NT>(b, l, 0.0) - om * db) / b.w[j];
       }
     }
   }

@@ -4,6 +4,8 @@
 // helpers.  Reductions are two-stage with a fixed summation order, so every
 // result is bit-reproducible run to run.
 #include "dfloat.cuh"
+#include <type_traits>
+
 #include "fields.cuh"
 
 namespace sldg {
@@ -58,7 +60,9 @@ __device__ void block_ksum(KSum (&k)[M], KSum* shm /* 32*M */) {
 // Projection matrices (Eq. (AB-sldg)) for count shifts a_e = src[e]*dt*frac:
 // x-sweeps take src = v-node coordinates, v-sweeps src = E at the x-nodes.
 // ---------------------------------------------------------------------------
-template <typename T>
+// NT: the node count b.n as a compile-time constant (the construction's
+// loops unroll and its arrays stay in registers)
+template <typename T, int NT>
 __global__ void k_build_mats(long long count, const double* __restrict__ src, double dt,
                              double frac, double h, Basis b, T* __restrict__ ab,
                              T* __restrict__ dab, float2* __restrict__ ab2,
@@ -73,8 +77,9 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
   split_shift(a, h, &s, &theta);
   double A[kMaxNodes * kMaxNodes], B[kMaxNodes * kMaxNodes];
   double dA[kMaxNodes * kMaxNodes], dB[kMaxNodes * kMaxNodes];
-  build_ab(b, theta, A, B, dab ? dA : nullptr, dab ? dB : nullptr);
-  const int nn = b.n * b.n;
+  build_ab<NT>(b, theta, A, B, dab ? dA : nullptr, dab ? dB : nullptr);
+  constexpr int nn = NT * NT;
+#pragma unroll
   for (int i = 0; i < nn; ++i) {
     ab[(long long)i * count + e] = (T)A[i];
     ab[(long long)(nn + i) * count + e] = (T)B[i];
@@ -93,8 +98,8 @@ __global__ void k_build_mats(long long count, const double* __restrict__ src, do
       }
     }
     if (abt) {  // [B^T; A^T]: entry i = j n + l holds B[l][j], then A[l][j]
-      const int j = i / b.n, l = i - j * b.n;
-      const double bt = B[l * b.n + j], at = A[l * b.n + j];
+      const int j = i / NT, l = i - j * NT;
+      const double bt = B[l * NT + j], at = A[l * NT + j];
       abt[(long long)i * count + e] = (T)bt;
       abt[(long long)(nn + i) * count + e] = (T)at;
       if (abt2) {
@@ -561,15 +566,25 @@ cudaError_t launch_build_mats(int prec, long long count, const double* src, doub
                               double h, const Basis& b, void* ab, void* dab, void* ab2, int* s,
                               cudaStream_t st, void* abt, void* abt2, int* sT, void* dab2) {
   if (count <= 0) return cudaSuccess;
-  if (prec == SLDG_FP64)
-    k_build_mats<double><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
-                                                           (double*)ab, (double*)dab,
-                                                           (float2*)ab2, s, (double*)abt,
-                                                           (float2*)abt2, sT, (float2*)dab2);
-  else
-    k_build_mats<float><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b, (float*)ab,
-                                                          (float*)dab, nullptr, s, (float*)abt,
-                                                          nullptr, sT, nullptr);
+  auto go = [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    if (prec == SLDG_FP64)
+      k_build_mats<double, NT><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
+                                                                 (double*)ab, (double*)dab,
+                                                                 (float2*)ab2, s, (double*)abt,
+                                                                 (float2*)abt2, sT, (float2*)dab2);
+    else
+      k_build_mats<float, NT><<<nblk(count, 32), 32, 0, st>>>(count, src, dt, frac, h, b,
+                                                                (float*)ab, (float*)dab, nullptr,
+                                                                s, (float*)abt, nullptr, sT, nullptr);
+  };
+  switch (b.n) {
+    case 1: go(std::integral_constant<int, 1>()); break;
+    case 2: go(std::integral_constant<int, 2>()); break;
+    case 3: go(std::integral_constant<int, 3>()); break;
+    case 4: go(std::integral_constant<int, 4>()); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
