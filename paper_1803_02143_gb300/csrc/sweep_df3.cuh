@@ -681,9 +681,9 @@ cudaError_t launch_x1_warp_T(const SweepArgs& a, cudaStream_t st) {
 // a fixed order.
 // ---------------------------------------------------------------------------
 template <int N>
-inline size_t ebar_df3_smem(long long D, bool fuse = false) {
+inline size_t ebar_df3_smem(long long D, bool fuse = false, int nbuf = 1) {
   return (fuse ? 2 : 1) * (size_t)kDf3Pairs * df3_mat_stride<N>() * sizeof(float4) +
-         2 * (size_t)(D + N) * kStridedW * sizeof(double) +
+         2 * (size_t)nbuf * (D + N) * kStridedW * sizeof(double) +
          (size_t)kDf3Groups * kStridedW * sizeof(double);
 }
 
@@ -697,7 +697,8 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
     k_ebar_df3(double* lam, const double* __restrict__ gf,
                double* __restrict__ epart, int ncols, long long rstride, long long ostride, int nc,
                int outer, const float2* __restrict__ dab2, const int* __restrict__ svec,
-               long long mcount, const float2* __restrict__ tab2, const int* __restrict__ tsvec) {
+               long long mcount, const float2* __restrict__ tab2, const int* __restrict__ tsvec,
+               int nbuf) {
   constexpr int W = kStridedW;
   constexpr int MN = 2 * N * N;
   constexpr int MS = df3_mat_stride<N>();
@@ -706,10 +707,11 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
   float4* tmat = smat + (FUSE ? kDf3Pairs * MS : 0);  // transposed tables (FUSE)
   const int D = nc * N;
   const int bstride = (D + N) * W;
-  double* tl = reinterpret_cast<double*>(smraw + (size_t)(FUSE ? 2 : 1) * kDf3Pairs * MS *
-                                                      sizeof(float4));
-  double* tg = tl + bstride;
-  double* red = tg + bstride;  // [groups][W]
+  // nbuf (1 or 2) pairs of tile buffers (adjoint, forward input): with two,
+  // the next tile is staged by cp.async while the current one is computed
+  double* bufs = reinterpret_cast<double*>(smraw + (size_t)(FUSE ? 2 : 1) * kDf3Pairs * MS *
+                                                        sizeof(float4));
+  double* red = bufs + 2 * nbuf * bstride;  // [groups][W]
   const int col0 = blockIdx.x * W;
   const int nvalid = min(W, ncols - col0);
   const int q = threadIdx.x % kDf3Pairs, g = threadIdx.x / kDf3Pairs;
@@ -740,10 +742,10 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
     ta0 = wrap_cell(ta0, nc);
     ta1 = wrap_cell(ta1, nc);
   }
-  if (!PERIODIC)
-    for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
-      tg[D * W + i] = 0.0;
-      if (FUSE) tl[D * W + i] = 0.0;  // the zero-inflow cell of the transposed sweep
+  if (!PERIODIC)  // the zero-inflow cell rows of every buffer (never loaded)
+    for (int i = threadIdx.x; i < 2 * nbuf * N * W; i += blockDim.x) {
+      const int t = i / (N * W);
+      bufs[t * bstride + D * W + (i - t * N * W)] = 0.0;
     }
   const float4* M = smat + q * MS;
   const int chunks = D * (W / 2);
@@ -752,20 +754,31 @@ __global__ void __launch_bounds__(kDf3Threads, 2)
     if (PERIODIC) return k;
     return (unsigned)k < (unsigned)nc ? k : nc;
   };
-  for (int o = blockIdx.y; o < outer; o += gridDim.y) {
-    const long long base = (long long)o * ostride + col0;
+  auto issue = [&](int o, double* xl, double* xg) {
+    const long long bo = (long long)o * ostride + col0;
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
       const int r = i / (W / 2), cq = i - r * (W / 2);
       if (cq < vchunks) {
-        cp_async16(tl + r * W + 2 * cq, lam + base + r * rstride + 2 * cq);
-        cp_async16(tg + r * W + 2 * cq, gf + base + r * rstride + 2 * cq);
+        cp_async16(xl + r * W + 2 * cq, lam + bo + r * rstride + 2 * cq);
+        cp_async16(xg + r * W + 2 * cq, gf + bo + r * rstride + 2 * cq);
       }
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (nbuf == 2 && (int)blockIdx.y < outer) issue(blockIdx.y, bufs, bufs + bstride);
+  int b = 0;
+  for (int o = blockIdx.y; o < outer; o += gridDim.y, b ^= 1) {
+    const long long base = (long long)o * ostride + col0;
+    double* tl = bufs + (nbuf == 2 ? b : 0) * 2 * bstride;
+    double* tg = tl + bstride;
+    if (nbuf == 1) issue(o, tl, tg);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     df3_pair_planar<false>(tl, D * (W / 2));
     df3_pair_planar<G_DF>(tg, D * (W / 2));
     __syncthreads();
+    if (nbuf == 2 && o + (int)gridDim.y < outer)
+      issue(o + gridDim.y, bufs + (b ^ 1) * 2 * bstride, bufs + (b ^ 1) * 2 * bstride + bstride);
     float2 ph = make_float2(0.0f, 0.0f), pl = make_float2(0.0f, 0.0f);  // per-lane partial
     bool first = true;
     if (active) {
@@ -844,7 +857,9 @@ cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
       ((reinterpret_cast<uintptr_t>(lam) | reinterpret_cast<uintptr_t>(gf)) & 15) ||
       ncols > 0x7fffffffLL - kStridedW || outer > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
     return cudaErrorNotSupported;
-  const size_t smem = ebar_df3_smem<N>(D, fuse);
+  // two buffer pairs while two CTAs still fit on an SM, else one
+  int nbuf = ebar_df3_smem<N>(D, fuse, 2) <= 113 * 1024 ? 2 : 1;
+  const size_t smem = ebar_df3_smem<N>(D, fuse, nbuf);
   if (smem > 113 * 1024) return cudaErrorNotSupported;
   const long long ncolblk = (ncols + kStridedW - 1) / kStridedW;
   long long gy = (outer + kDf3TilesPerCtaV - 1) / kDf3TilesPerCtaV;
@@ -860,7 +875,7 @@ cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
   kfn<<<dim3((unsigned)ncolblk, (unsigned)gy), kDf3Threads, smem, st>>>(
       lam, gf, a.epart, (int)ncols, rstride, ostride, a.nc, (int)outer,
       reinterpret_cast<const float2*>(a.dab2), a.s, a.mcount,
-      reinterpret_cast<const float2*>(a.tab2), a.ts);
+      reinterpret_cast<const float2*>(a.tab2), a.ts, nbuf);
   return cudaGetLastError();
 }
 
