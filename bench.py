@@ -228,7 +228,7 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
                "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active")
 
 # translation unit of each kernel family (its sources key the traffic entry)
-KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
+KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df_x12.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
                 ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),
                 ("k_sweep_strided_f2", "sweep_f32.cu"), ("k_sweep_x1_f2warp", "sweep_f32.cu"),
                 ("k_rho_partial", "fields.cu"), ("k_spline_sweep", "spline.cu"))
@@ -629,27 +629,44 @@ def run_e2e(s, w, steps):
     s.get_f(host)
     s.step_host_batches(host, 2)  # warm
     torch.cuda.synchronize()
+    # the host link's rate right now: one plain upload of the same buffer
+    # (f already holds these values); the steps cannot run faster than
+    # their uploads
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.f.copy_(host, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    esize = 8 if s.cfg.precision == "fp64" else 4
+    up_bytes = s.cfg.numel * esize
     t0 = time.perf_counter()
     W = s.step_host_batches(host, steps)
     t1 = time.perf_counter()
-    esize = 8 if s.cfg.precision == "fp64" else 4
     return {"value": s.cfg.numel * steps / (t1 - t0), "unit": UNIT,
-            "h2d_bytes_per_step": s.cfg.numel * esize, "d2h_bytes_per_step": 8,
+            "h2d_bytes_per_step": up_bytes, "d2h_bytes_per_step": 8,
             "ms_per_step": 1e3 * (t1 - t0) / steps, "steps": steps,
+            "h2d_gbps_copy_alone": up_bytes / (e0.elapsed_time(e1) * 1e6),
+            "h2d_gbps_in_steps": up_bytes * steps / ((t1 - t0) * 1e9),
             "last_W": float(W[-1])}
 
 
 def run_adjoint_ratio():
     """Adjoint/forward wall ratio on the adjoint workload (32^4, degree 1, 100
-    steps, checkpoint every 10): record+backward vs a plain forward."""
+    steps, checkpoint every 10): record+backward vs a plain forward, each
+    timed after an untimed pass of all three."""
     import torch
 
     from paper_1803_02143_gb300 import Sldg, configs
 
     w = configs.workload("adjoint_landau_32")
     s = Sldg(w.cfg)
+    # one untimed pass of each phase: tables, replay graphs and the
+    # recording's and backward's buffers exist before the timed passes
     s.set_initial(w.kind, w.params)
-    s.step(2)
+    s.step(w.steps)
+    s.set_initial(w.kind, w.params)
+    s.record(w.steps, w.ckpt)
+    s.backward()
     torch.cuda.synchronize()
     s.set_initial(w.kind, w.params)
     t0 = time.perf_counter()

@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsldg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "fields.cu", "sweep_df.cu", "sweep_f64.cu", "sweep_f32.cu", "noalloc.cu",
-           "spline.cu"]
+SOURCES = ["api.cu", "fields.cu", "sweep_df.cu", "sweep_df_x12.cu", "sweep_df_adj.cu",
+           "sweep_f64.cu", "sweep_f32.cu", "noalloc.cu", "spline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 

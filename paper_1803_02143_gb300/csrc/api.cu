@@ -471,7 +471,7 @@ int compute_fields(sldg_ctx* c, const void* buf, bool df = false) {
 // ([B^T; A^T], shift entries -s - 1) like the separate adjoint x-sweeps
 // out (nullable): the result goes there and buf is left unchanged
 int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* done,
-            bool trans = false, void* out = nullptr) {
+            bool trans = false, void* out = nullptr, bool rho_fold = false) {
   *done = false;
   if (c->cfg.flags & (SLDG_FLAG_NO_XFUSION | SLDG_FLAG_NATIVE_FP64 | SLDG_FLAG_SPLINE))
     return SLDG_OK;
@@ -481,13 +481,16 @@ int run_x12(sldg_ctx* c, void* buf, double frac, bool in_df, bool out_df, bool* 
   const int* s0 = trans ? m0->st : m0->s;
   const int* s1 = trans ? m1->st : m1->s;
   KTimer t(c, trans ? SLDG_K_ADJ_X : SLDG_K_X12);
+  const double* fw = rho_fold ? c->d_wv : nullptr;
+  const double* fr = rho_fold ? c->d_rhob : nullptr;
   const cudaError_t e =
       c->prec == SLDG_FP32
           ? launch_sweep_x12_f32(buf, c->g, trans ? m0->abt : m0->ab, s0,
-                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape, out)
+                                 trans ? m1->abt : m1->ab, s1, c->stream, c->x12_shape, out, fw,
+                                 fr)
           : launch_sweep_x12_df(buf, c->g, trans ? m0->abt2 : m0->ab2, s0,
                                 trans ? m1->abt2 : m1->ab2, s1, in_df ? 1 : 0, out_df ? 1 : 0,
-                                c->stream, c->x12_shape, out);
+                                c->stream, c->x12_shape, out, fw, fr);
   if (e == cudaErrorNotSupported) {
     t.n = 0;  // nothing launched
     return SLDG_OK;
@@ -1160,6 +1163,16 @@ int sldg_diagnostics(sldg_ctx* c, sldg_diag* out) {
 }
 
 // ---- adjoint ------------------------------------------------------------------------
+// The backward's state-sized working memory: the recomputation slots, the
+// intermediates of an adjoint step and the recomputed kick fields
+static void release_backward_scratch(sldg_ctx* c) {
+  dfree(c->d_seg);
+  c->seg_count = 0;
+  for (int i = 0; i < 2; ++i) dfree(c->d_work[i]);
+  dfree(c->d_Ecap);
+  c->Ecap_steps = 0;
+}
+
 static int ensure_adjoint_scratch(sldg_ctx* c) {
   const Grid& g = c->g;
   for (int d = 0; d < 2; ++d)
@@ -1191,14 +1204,25 @@ int sldg_record(sldg_ctx* c, int nsteps, int ckpt_every, double* W_history) {
   if (nsteps < 1 || ckpt_every < 1) return SLDG_ERR_ARG;
   const size_t fb = c->g.N * c->esize;
   const size_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
-  dfree(c->d_ckpool);
-  dfree(c->d_seg);
-  for (int i = 0; i < 2; ++i) dfree(c->d_work[i]);
-  dfree(c->d_Wrec);
-  c->seg_count = 0;
   c->recorded = false;
-  SLDG_TRY(dalloc(&c->d_ckpool, nck * fb));
-  SLDG_TRY(dalloc(&c->d_Wrec, nsteps * sizeof(double)));
+  // the pool, the W history and the backward's working copies stay allocated
+  // between recordings (the replayed step graph keeps its W buffer); a pool
+  // that does not fit beside the backward's copies takes their memory
+  if (c->ck_cap < nck) {
+    dfree(c->d_ckpool);
+    c->ck_cap = 0;
+    if (dalloc(&c->d_ckpool, nck * fb) != SLDG_OK) {
+      release_backward_scratch(c);
+      SLDG_TRY(dalloc(&c->d_ckpool, nck * fb));
+    }
+    c->ck_cap = nck;
+  }
+  if (c->Wrec_cap < nsteps) {
+    dfree(c->d_Wrec);
+    c->Wrec_cap = 0;
+    SLDG_TRY(dalloc(&c->d_Wrec, nsteps * sizeof(double)));
+    c->Wrec_cap = nsteps;
+  }
   c->ck_count = nck;
   c->rec_t0 = c->t;
   c->rec_step0 = c->step;
@@ -1273,11 +1297,18 @@ namespace {
 // transposed, the v-shift derivatives, the Poisson and charge-density
 // adjoints).
 // Adjoint of a half drift X2(tau/2) X1(tau/2) on the adjoint in place: one
-// fused pass of the transposed sweeps, or X2^T then X1^T
-int adjoint_drift(sldg_ctx* c, void* lam) {
+// fused pass of the transposed sweeps, or X2^T then X1^T.  rho_fold: first
+// the charge-density adjoint lam += w_v rho_bar(x) (the adjoint of the
+// density the drift's output fed), inside the fused pass's staging or as
+// its own kernel
+int adjoint_drift(sldg_ctx* c, void* lam, bool rho_fold = false) {
   bool fused = false;
-  SLDG_TRY(run_x12(c, lam, 0.5, false, false, &fused, true));
+  SLDG_TRY(run_x12(c, lam, 0.5, false, false, &fused, true, nullptr, rho_fold));
   if (!fused) {
+    if (rho_fold) {
+      KTimer t(c, SLDG_K_RHO);
+      SLDG_CU(launch_rho_adj(c->prec, lam, c->g, c->d_wv, c->d_rhob, c->stream));
+    }
     SLDG_TRY(run_sweep(c, lam, 1, 0.5, true, nullptr, nullptr));
     SLDG_TRY(run_sweep(c, lam, 0, 0.5, true, nullptr, nullptr));
   }
@@ -1311,11 +1342,7 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
     KTimer t(c, SLDG_K_POISSON, 4);
     SLDG_CU(launch_poisson_adj(poisson_args(c), c->d_Eb[0], c->d_Eb[1], c->d_rhob, c->stream, &nl));
   }
-  {
-    KTimer t(c, SLDG_K_RHO);
-    SLDG_CU(launch_rho_adj(c->prec, grad, g, c->d_wv, c->d_rhob, c->stream));
-  }
-  return adjoint_drift(c, grad);
+  return adjoint_drift(c, grad, true);
 }
 
 // The same from the step's initial state fm (recomputing g2, g3 and the

@@ -84,15 +84,20 @@ cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st);
 // fused X1, X2 of FP32 storage (sweep_f32.cu); cudaErrorNotSupported if the
 // layout does not fit.  shape (nullable, two ints): the launch's CTAs per
 // x-plane (cluster size) and lanes per x1 line pair of its X1 phase.  out
-// (nullable): write the result there and leave f unchanged.
+// (nullable): write the result there and leave f unchanged.  fold_w, fold_r
+// (nullable): first add fold_w[v] * fold_r[x] to every input element (the
+// charge-density adjoint ahead of a transposed pass, as launch_rho_adj).
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
                                  const void* ab2, const int* s2, cudaStream_t st,
-                                 int* shape = nullptr, void* out = nullptr);
-// the same for FP64 storage in double-float arithmetic (sweep_df.cu); ab1, ab2
-// are the (hi, lo) float-pair tables, in_df / out_df the element formats
+                                 int* shape = nullptr, void* out = nullptr,
+                                 const double* fold_w = nullptr, const double* fold_r = nullptr);
+// the same for FP64 storage in double-float arithmetic (sweep_df_x12.cu); ab1, ab2
+// are the (hi, lo) float-pair tables, in_df / out_df the element formats (the
+// fold takes IEEE inputs only: cudaErrorInvalidValue with in_df)
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
-                                cudaStream_t st, int* shape = nullptr, void* out = nullptr);
+                                cudaStream_t st, int* shape = nullptr, void* out = nullptr,
+                                const double* fold_w = nullptr, const double* fold_r = nullptr);
 size_t sweep_smem_bytes(int prec, int dim, long long D, int lines_per_tile);
 // SLDG_OK or SLDG_ERR_BAD_CONFIG: the configuration checks of sldg_init (api.cu)
 int validate_config(const sldg_config* cfg);
@@ -149,11 +154,12 @@ struct sldg_ctx {
   double* d_diag = nullptr;  // small result buffer
 
   // adjoint
-  void* d_ckpool = nullptr;  // checkpoints
-  size_t ck_count = 0;
+  void* d_ckpool = nullptr;  // checkpoints: ck_count in use of ck_cap allocated
+  size_t ck_count = 0, ck_cap = 0;
   int rec_nsteps = 0, rec_ckpt = 0;
   bool recorded = false;
-  double* d_Wrec = nullptr;
+  double* d_Wrec = nullptr;  // recorded W history, Wrec_cap doubles allocated
+  int Wrec_cap = 0;
   void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};  // g2, g3 of the adjoint step
   void* d_seg = nullptr;        // recomputation slots, seg_count states of f
   size_t seg_count = 0;

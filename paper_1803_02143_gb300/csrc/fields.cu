@@ -532,7 +532,7 @@ __global__ void k_rho_adj(T* __restrict__ lam, long long N, long long Dx,
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const long long p = i % Dx, v = i / Dx;
-    lam[i] = (T)((double)lam[i] + wv[v] * rhob[p]);
+    lam[i] = (T)fma(wv[v], rhob[p], (double)lam[i]);  // as the fused x passes' fold
   }
 }
 

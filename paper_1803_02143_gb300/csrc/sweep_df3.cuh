@@ -196,7 +196,7 @@ __device__ __forceinline__ void df3_run(const double* __restrict__ raw, const fl
 // the current one is computed; two CTAs per SM (105 KB of shared memory per
 // CTA for 192-node lines).  Longer lines use one buffer.
 template <int N, bool PERIODIC, bool PERCOL, bool IN_DF, bool OUT_DF>
-__global__ void __launch_bounds__(kDf3Threads, 2)
+__global__ void __launch_bounds__(kDf3Threads, N <= 2 ? 3 : 2)
     k_sweep_strided_df3(const double* f, double* out, int ncols, long long rstride, long long ostride,
                         int nc, int outer, int nbuf, const float2* __restrict__ ab2,
                         const int* __restrict__ svec, long long mcount, int key_div, int key_mod) {
@@ -693,7 +693,7 @@ inline size_t ebar_df3_smem(long long D, bool fuse = false, int nbuf = 1) {
 // shifts -s - 1) and writes it back to lam, so the adjoint is read once for
 // both.
 template <int N, bool PERIODIC, bool G_DF, bool FUSE>
-__global__ void __launch_bounds__(kDf3Threads, 2)
+__global__ void __launch_bounds__(kDf3Threads, N <= 2 ? 3 : 2)
     k_ebar_df3(double* lam, const double* __restrict__ gf,
                double* __restrict__ epart, int ncols, long long rstride, long long ostride, int nc,
                int outer, const float2* __restrict__ dab2, const int* __restrict__ svec,

@@ -14,14 +14,14 @@ cudaError_t launch_sweep_f32(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const int* s1,
                                  const void* ab2, const int* s2, cudaStream_t st, int* shape,
-                                 void* out) {
+                                 void* out, const double* fold_w, const double* fold_r) {
   const float* ff = static_cast<const float*>(f);
   float* o = static_cast<float*>(out ? out : f);
   switch (g.n) {
-    case 1: return launch_x12_N<1>(ff, o, g, ab1, s1, ab2, s2, st, shape);
-    case 2: return launch_x12_N<2>(ff, o, g, ab1, s1, ab2, s2, st, shape);
-    case 3: return launch_x12_N<3>(ff, o, g, ab1, s1, ab2, s2, st, shape);
-    case 4: return launch_x12_N<4>(ff, o, g, ab1, s1, ab2, s2, st, shape);
+    case 1: return launch_x12_N<1>(ff, o, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
+    case 2: return launch_x12_N<2>(ff, o, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
+    case 3: return launch_x12_N<3>(ff, o, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
+    case 4: return launch_x12_N<4>(ff, o, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
     default: return cudaErrorNotSupported;
   }
 }

@@ -66,11 +66,14 @@ __host__ __device__ __forceinline__ int x12_lanes_per_pair(int nc0, int cpl) {
 
 // CPL: cells of an x1 line per lane (nc0 <= 32 CPL); GRP: several lane
 // groups per warp in the X1 phase (lines of at most 16 CPL cells)
-template <int N, int CPL, bool GRP>
+// FOLD: add fold_w[v] fold_r[x] to the staged input first (the transposed
+// passes of the adjoint)
+template <int N, int CPL, bool GRP, bool FOLD>
 __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     k_sweep_x12_f32(const float* src, float* dst, int nc0, int nc1, int cs, int run, int D2, int D3,
                     const float* __restrict__ ab1, const int* __restrict__ s1,
-                    const float* __restrict__ ab2, const int* __restrict__ s2) {
+                    const float* __restrict__ ab2, const int* __restrict__ s2,
+                    const double* __restrict__ fold_w, const double* __restrict__ fold_r) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* rows = reinterpret_cast<float*>(smraw);
@@ -89,6 +92,16 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
     const int chunks = H * D0 / 4;
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 4 * i, sp + 4 * i);
     cp_async_wait_all();
+    if (FOLD) {
+      // the charge-density adjoint folded in: rows += w_v rho_bar(x) in FP64
+      // (the operation of k_rho_adj), each thread on the chunks it copied
+      const double w = fold_w[plane];
+      const double* r = fold_r + (long long)rank * H * D0;
+      for (int i = threadIdx.x; i < chunks; i += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          rows[4 * i + j] = (float)fma(w, r[4 * i + j], (double)rows[4 * i + j]);
+    }
   }
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
   __syncthreads();
@@ -234,9 +247,10 @@ __global__ void __launch_bounds__(kX12Threads, N >= 4 && CPL >= 4 ? 2 : 3)
 // layout does not fit (the caller then runs the two sweeps).
 template <int N, int CPL>
 cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
-                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape,
+                         const double* fold_w, const double* fold_r) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
-  const long long D0 = (long long)nc0 * N, D1 = (long long)nc1 * N;
+  const long long D0 = (long long)nc0 * N;
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 4 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
     return cudaErrorNotSupported;
@@ -256,8 +270,9 @@ cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* 
   const size_t smem = (size_t)(nc1 / cs) * N * D0 * sizeof(float);
   const int cells_per = nc1 / cs;
   const int run = std::max(1, (cells_per + kX12Groups - 1) / kX12Groups);  // cells per X2 item
-  auto kfn = x12_lanes_per_pair(nc0, CPL) < 32 ? k_sweep_x12_f32<N, CPL, true>
-                                               : k_sweep_x12_f32<N, CPL, false>;
+  const bool grp = x12_lanes_per_pair(nc0, CPL) < 32;
+  auto kfn = grp ? k_sweep_x12_f32<N, CPL, true, false> : k_sweep_x12_f32<N, CPL, false, false>;
+  if (fold_w) kfn = grp ? k_sweep_x12_f32<N, CPL, true, true> : k_sweep_x12_f32<N, CPL, false, true>;
   cudaError_t e = set_smem(kfn, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -277,15 +292,17 @@ cudaError_t launch_x12_T(const float* f, float* out, const Grid& g, const void* 
     shape[1] = x12_lanes_per_pair(nc0, CPL);
   }
   return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
-                            static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2);
+                            static_cast<const float*>(ab1), s1, static_cast<const float*>(ab2), s2,
+                            fold_w, fold_r);
 }
 
 template <int N>
 cudaError_t launch_x12_N(const float* f, float* out, const Grid& g, const void* ab1, const int* s1,
-                         const void* ab2, const int* s2, cudaStream_t st, int* shape) {
+                         const void* ab2, const int* s2, cudaStream_t st, int* shape,
+                         const double* fold_w, const double* fold_r) {
   const int nc0 = g.nc[0];
-  if (nc0 <= 64) return launch_x12_T<N, 2>(f, out, g, ab1, s1, ab2, s2, st, shape);
-  if (nc0 <= 128) return launch_x12_T<N, 4>(f, out, g, ab1, s1, ab2, s2, st, shape);
+  if (nc0 <= 64) return launch_x12_T<N, 2>(f, out, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
+  if (nc0 <= 128) return launch_x12_T<N, 4>(f, out, g, ab1, s1, ab2, s2, st, shape, fold_w, fold_r);
   return cudaErrorNotSupported;
 }
 

@@ -40,7 +40,8 @@ template <int N, int CPL, bool GRP, bool IN_DF, bool OUT_DF>
 __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
     k_sweep_x12_df(const double* src, double* dst, int nc0, int nc1, int cs, int run, int D2, int D3,
                    const float2* __restrict__ ab1, const int* __restrict__ s1,
-                   const float2* __restrict__ ab2, const int* __restrict__ s2) {
+                   const float2* __restrict__ ab2, const int* __restrict__ s2,
+                   const double* __restrict__ fold_w, const double* __restrict__ fold_r) {
   constexpr int MN = 2 * N * N;
   extern __shared__ __align__(16) unsigned char smraw[];
   float4* m1 = reinterpret_cast<float4*>(smraw);
@@ -55,9 +56,9 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
   double* op = dst + plane * (long long)D1 * D0;        // written (may be fp)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
+  const int chunks = H * D0 / 2;
   {
     const double* sp = fp + (long long)rank * H * D0;
-    const int chunks = H * D0 / 2;
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(rows + 2 * i, sp + 2 * i);
   }
   const int key1 = (int)(plane % D2), key2 = (int)((plane / D2) % D3);
@@ -67,6 +68,16 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
     m2[i] = make_float4(b.x, b.x, b.y, b.y);
   }
   cp_async_wait_all();
+  if (!IN_DF && fold_w) {
+    // the charge-density adjoint folded in: rows += w_v rho_bar(x) (the
+    // operation of k_rho_adj), each thread on the chunks it copied
+    const double w = fold_w[plane];
+    const double* r = fold_r + (long long)rank * H * D0;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+      rows[2 * i] = fma(w, r[2 * i], rows[2 * i]);
+      rows[2 * i + 1] = fma(w, r[2 * i + 1], rows[2 * i + 1]);
+    }
+  }
   __syncthreads();
 
   // X1 in place, a lane group per row pair (several groups per warp on short
@@ -209,12 +220,13 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
 template <int N, int CPL, bool IN_DF, bool OUT_DF>
 cudaError_t launch_x12_df_T(const double* f, double* out, const Grid& g, const void* ab1,
                             const int* s1, const void* ab2, const int* s2, cudaStream_t st,
-                            int* shape) {
+                            int* shape, const double* fold_w, const double* fold_r) {
   const int nc0 = g.nc[0], nc1 = g.nc[1];
   const long long D0 = (long long)nc0 * N;
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 2 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
     return cudaErrorNotSupported;
+  if (fold_w && IN_DF) return cudaErrorInvalidValue;  // the fold adds to IEEE inputs only
   const size_t mats = 2 * (size_t)(2 * N * N) * sizeof(float4);
   // the smallest cluster (2 to 8 CTAs) whose row share fits six CTAs per SM,
   // else the largest that fits one
@@ -256,15 +268,16 @@ cudaError_t launch_x12_df_T(const double* f, double* out, const Grid& g, const v
   }
   return cudaLaunchKernelEx(&cfg, kfn, f, out, nc0, nc1, cs, run, (int)g.D[2], (int)g.D[3],
                             static_cast<const float2*>(ab1), s1, static_cast<const float2*>(ab2),
-                            s2);
+                            s2, fold_w, fold_r);
 }
 
 template <int N, bool IN_DF, bool OUT_DF>
 cudaError_t launch_x12_df_N(const double* f, double* out, const Grid& g, const void* ab1,
                             const int* s1, const void* ab2, const int* s2, cudaStream_t st,
-                            int* shape) {
+                            int* shape, const double* fold_w, const double* fold_r) {
   if (g.nc[0] <= 64)
-    return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, out, g, ab1, s1, ab2, s2, st, shape);
+    return launch_x12_df_T<N, 2, IN_DF, OUT_DF>(f, out, g, ab1, s1, ab2, s2, st, shape, fold_w,
+                                                fold_r);
   return cudaErrorNotSupported;
 }
 

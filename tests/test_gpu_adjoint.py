@@ -186,3 +186,33 @@ def test_checkpoint_pool_beyond_hbm_is_oom_and_context_survives(lib, orc):
     J, grad = s.backward()
     assert np.isfinite(W).all() and np.isfinite(J) and torch.isfinite(grad).all()
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_recordings_reuse_their_buffers(lib, prec):
+    """A context keeps its checkpoint pool, W history and backward copies
+    between recordings: recordings of other lengths in between (a smaller
+    pool, then a larger one) leave J and the gradient of a recording
+    bit-identical to those of a fresh context."""
+    from inputs import LANDAU_HI, LANDAU_LO
+
+    cfg = lib.Config(degree=2, ncell=(8, 6, 10, 12), lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1,
+                     precision=prec)
+    params = (0.5, 0.5, 0.5)
+
+    def run(s, n, ck):
+        s.set_initial(0, params)
+        W = s.record(n, ck)
+        J, g = s.backward()
+        torch.cuda.synchronize()
+        return W.copy(), J, g.clone()
+
+    with lib.Sldg(cfg) as fresh:
+        W0, J0, g0 = run(fresh, 12, 4)
+    with lib.Sldg(cfg) as s:
+        run(s, 12, 4)
+        run(s, 5, 2)    # the pool and the W history are larger than needed
+        run(s, 30, 3)   # both grow
+        W1, J1, g1 = run(s, 12, 4)
+    assert np.array_equal(W0, W1) and J0 == J1
+    assert torch.equal(g0, g1)

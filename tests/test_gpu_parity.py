@@ -244,24 +244,34 @@ def test_fp32_energy_history(lib, orc):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64"])
-def test_backward_matches_oracle(lib, orc, prec):
-    s, og = make(lib, orc, 1, (6, 5, 8, 7), dt=0.1, prec=prec)
+# Unfused (SLDG_FLAG_NO_XFUSION, and odd nc1 in FP64): every x drift and its
+# adjoint as separate sweeps, the charge-density adjoint as its own kernel;
+# fused: the transposed x pass adds the charge-density adjoint while it
+# stages its planes.  FP32: 7 steps of 6 transposed sweeps and their
+# recomputation, each within the one-sweep bound 3e-6 of the oracle.
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("deg,nc,fused", [(1, (6, 5, 8, 7), False), (1, (8, 6, 5, 4), False),
+                                          (1, (8, 6, 5, 4), True), (2, (8, 8, 4, 3), True)])
+def test_backward_matches_oracle(lib, orc, prec, deg, nc, fused):
+    flags = 0 if fused else lib._native.SLDG_FLAG_NO_XFUSION
+    s, og = make(lib, orc, deg, nc, dt=0.1, prec=prec, flags=flags)
+    tol = {"W": 1e-12, "grad": 1e-11} if prec == "fp64" else {"W": 1e-5, "grad": 1e-4}
     params = (0.5, 0.5, 0.5)
     s.set_initial(0, params)
     f0 = orc.init(og, 0, params)
     n, ck = 7, 3
     W = s.record(n, ck)
     J, grad = s.backward()
+    assert (s.x_pass_shape[0] > 0) == fused
     Jr, gr, Wr = orc.backward(og, f0, n, ck)
-    assert relerr(W, Wr) < 1e-12
-    assert abs(J - Jr) < 1e-12 * abs(Jr)
+    assert relerr(W, Wr) < tol["W"]
+    assert abs(J - Jr) < tol["W"] * abs(Jr)
     torch.cuda.synchronize()
-    assert relerr(grad.cpu().numpy(), gr.reshape(og.shape)) < 1e-11
+    assert relerr(grad.double().cpu().numpy(), gr.reshape(og.shape)) < tol["grad"]
     # dJ/deps through the library's reduction
     dfde = orc.init(og, 0, (1.0, 0.5, 0.5)) - orc.init(og, 0, (0.0, 0.5, 0.5))
     ge = s.initial_param_grad(0, params, grad)
-    assert abs(ge - np.sum(gr * dfde)) < 1e-11 * abs(ge)
+    assert abs(ge - np.sum(gr * dfde)) < tol["grad"] * abs(ge)
     s.close()
 
 
