@@ -228,6 +228,12 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
                "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active")
 
 # translation unit of each kernel family (its sources key the traffic entry)
+# (workload, precision, kind) whose launches run another kernel than the
+# capture case: FP32 v-sweeps of 384-value lines exceed the packed tile and
+# run the one-lane kernel, while the 48-value lines of the capture run the
+# packed one
+NCU_NOT_SCALED = {("two_stream_64x128", "fp32", "v1"), ("two_stream_64x128", "fp32", "v2")}
+
 KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df_x12.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
                 ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),
                 ("k_sweep_strided_f2", "sweep_f32.cu"), ("k_sweep_x1_f2warp", "sweep_f32.cu"),
@@ -362,7 +368,8 @@ def ingest_ncu(args):
         scale = tw.cfg.numel / case.cfg.numel
         for (prec, kind), vals in by_kind.items():
             unit = vals[0][1]
-            if unit is None:
+            if unit is None or (tname, prec, kind) in NCU_NOT_SCALED:
+                traffic.pop(f"{tname}:{prec}:{kind}", None)
                 continue
             b = sum(v for v, _ in vals) / len(vals)
             traffic[f"{tname}:{prec}:{kind}"] = {
