@@ -53,8 +53,9 @@ __global__ void k_spline_shifts(long long count, const double* __restrict__ src,
 // is the column (v-sweeps); otherwise the block (x-sweeps), key =
 // (block / key_div) % key_mod.  A CTA walks tiles tile0, tile0 + gridDim.x,
 // ...: with NB = 2 the next tile is staged by cp.async into the second
-// input buffer while the current one is computed (NB = 1: lines too long
-// for three [n][33] buffers stage each tile after the previous one).
+// input buffer while the current one is computed (NB = 1: each tile is
+// staged after the previous one, the overlap coming from the other CTAs
+// on the SM).
 template <typename T, bool CONTIG, bool KEYCOL, int NB>
 __global__ void __launch_bounds__(kSplThreads)
     k_spline_sweep(T* __restrict__ f, int n, long long inner, long long outer,
@@ -252,7 +253,11 @@ cudaError_t launch_spline_T(const SweepArgs& a, cudaStream_t st) {
   const int n = a.nc;
   const size_t buf = (size_t)n * kSplPitch * sizeof(T);
   if (n < 3 || 2 * buf > 227 * 1024) return cudaErrorNotSupported;
-  const int nb = 3 * buf <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
+  // two input buffers only where they cost no CTA (eight per SM still fit):
+  // at 128 points one buffer and more CTAs (six per SM in FP32, three in
+  // FP64) beat two buffers (four, two): 0.573 against 0.602 ms per FP32
+  // v-sweep and 4.88 against 5.12 ms per FP64 v-sweep at 128^4 points
+  const int nb = 8 * (3 * buf + 1024) <= 228 * 1024 ? 2 : 1;
   const size_t smem = (nb + 1) * buf;
   auto kfn = nb == 2 ? k_spline_sweep<T, CONTIG, KEYCOL, 2> : k_spline_sweep<T, CONTIG, KEYCOL, 1>;
   if (smem > 48 * 1024) {
