@@ -386,7 +386,8 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
     a.epart = c->d_epart;
   }
   const int kind = adjoint ? (dim < 2 ? SLDG_K_ADJ_X : SLDG_K_ADJ_V) : SLDG_K_X1 + dim;
-  bool swept = false;  // the transposed sweep ran with the partials
+  bool swept = false;      // the transposed sweep ran with the partials
+  bool lam_to_df = false;  // the IEEE fallback's result goes back to pairs
   if (ebar_df) {  // partials of d/dE <lam, S g> from the adjoint before the sweep
     KTimer t(c, kind);
     SweepArgs ae = a;
@@ -411,6 +412,13 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
         c->launches += 1;
         a.g_df = 0;
       }
+      if (a.in_df) {  // and the adjoint too, which it writes back as doubles
+        SLDG_CU(launch_df_to_ieee(buf, buf, g.N, c->stream));
+        c->launches += 1;
+      }
+      lam_to_df = a.out_df != 0;
+      a.in_df = 0;
+      a.out_df = 0;
     } else if (e != cudaSuccess) {
       cudaGetLastError();
       return SLDG_ERR_CUDA;
@@ -435,6 +443,10 @@ int run_sweep(sldg_ctx* c, void* buf, int dim, double frac, bool adjoint, const 
       cudaGetLastError();
       return SLDG_ERR_CUDA;
     }
+  }
+  if (lam_to_df) {
+    SLDG_CU(launch_ieee_to_df(buf, buf, g.N, c->stream));
+    c->launches += 1;
   }
   if (ebar) {
     // Ebar[x] += dt*frac/h_v * sum over the rows of partials at x
@@ -1296,21 +1308,33 @@ namespace {
 // grad <- (step m)^T grad + the dJ/dW_m c_m contributions (Eq. AB-sldg
 // transposed, the v-shift derivatives, the Poisson and charge-density
 // adjoints).
+// The backward keeps the adjoint in double-float pairs on FP64 storage with
+// double-float sweeps (no conversion through the FP64 pipe in its passes);
+// sldg_backward converts the gradient to IEEE doubles at the end.
+bool lam_df(const sldg_ctx* c) { return df_states(c); }
+
 // Adjoint of a half drift X2(tau/2) X1(tau/2) on the adjoint in place: one
 // fused pass of the transposed sweeps, or X2^T then X1^T.  rho_fold: first
 // the charge-density adjoint lam += w_v rho_bar(x) (the adjoint of the
 // density the drift's output fed), inside the fused pass's staging or as
-// its own kernel
+// its own kernel (on IEEE doubles)
 int adjoint_drift(sldg_ctx* c, void* lam, bool rho_fold = false) {
+  const bool ldf = lam_df(c);
   bool fused = false;
-  SLDG_TRY(run_x12(c, lam, 0.5, false, false, &fused, true, nullptr, rho_fold));
+  SLDG_TRY(run_x12(c, lam, 0.5, ldf, ldf, &fused, true, nullptr, rho_fold));
   if (!fused) {
+    bool in_df = ldf;
     if (rho_fold) {
+      if (in_df) {
+        KTimer t(c, SLDG_K_OTHER);
+        SLDG_CU(launch_df_to_ieee(lam, lam, c->g.N, c->stream));
+        in_df = false;
+      }
       KTimer t(c, SLDG_K_RHO);
       SLDG_CU(launch_rho_adj(c->prec, lam, c->g, c->d_wv, c->d_rhob, c->stream));
     }
-    SLDG_TRY(run_sweep(c, lam, 1, 0.5, true, nullptr, nullptr));
-    SLDG_TRY(run_sweep(c, lam, 0, 0.5, true, nullptr, nullptr));
+    SLDG_TRY(run_sweep(c, lam, 1, 0.5, true, nullptr, nullptr, in_df, ldf));
+    SLDG_TRY(run_sweep(c, lam, 0, 0.5, true, nullptr, nullptr, ldf, ldf));
   }
   return SLDG_OK;
 }
@@ -1330,8 +1354,9 @@ int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double*
   SLDG_CU(cudaMemsetAsync(c->d_Eb[1], 0, g.Dx * sizeof(double), c->stream));
   SLDG_TRY(adjoint_drift(c, grad));
   const bool gdf = df_states(c);  // g2, g3 as forward_stage keeps them
-  SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1], false, false, nullptr, gdf));
-  SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0], false, false, nullptr, gdf));
+  const bool ldf = lam_df(c);
+  SLDG_TRY(run_sweep(c, grad, 3, 1.0, true, g3, c->d_Eb[1], ldf, ldf, nullptr, gdf));
+  SLDG_TRY(run_sweep(c, grad, 2, 1.0, true, g2, c->d_Eb[0], ldf, ldf, nullptr, gdf));
   {
     KTimer t(c, SLDG_K_OTHER);
     SLDG_CU(launch_energy_adj(c->d_Eb[0], c->d_Eb[1], c->d_E[0], c->d_E[1], c->d_wx, g.Dx,
@@ -1505,6 +1530,10 @@ int sldg_backward(sldg_ctx* c, const double* cW, int ncW, void* grad, double* J_
   for (int sidx = nseg - 1; sidx >= 0; --sidx) {
     const int m0 = sidx * ck, m1 = std::min(m0 + ck, n);
     SLDG_TRY(adjoint_range(c, pool + (size_t)sidx * fb, m0, m1, free, cW, grad, false));
+  }
+  if (lam_df(c)) {  // the zero start reads as pairs; the result goes out as doubles
+    KTimer t(c, SLDG_K_OTHER);
+    SLDG_CU(launch_df_to_ieee(grad, grad, g.N, c->stream));
   }
   // the context's field now belongs to the first step; leave f as recorded
   c->have_field = false;

@@ -93,7 +93,7 @@ cudaError_t launch_sweep_x12_f32(void* f, const Grid& g, const void* ab1, const 
                                  const double* fold_w = nullptr, const double* fold_r = nullptr);
 // the same for FP64 storage in double-float arithmetic (sweep_df_x12.cu); ab1, ab2
 // are the (hi, lo) float-pair tables, in_df / out_df the element formats (the
-// fold takes IEEE inputs only: cudaErrorInvalidValue with in_df)
+// fold adds to either format)
 cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const int* s1,
                                 const void* ab2, const int* s2, int in_df, int out_df,
                                 cudaStream_t st, int* shape = nullptr, void* out = nullptr,

@@ -548,6 +548,15 @@ __global__ void k_energy_adj(double* __restrict__ Eb1, double* __restrict__ Eb2,
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
+// dst = the double-float pairs of the IEEE doubles in src (dst may be src)
+__global__ void k_ieee_to_df(const double* src, double* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 p = dsplit(src[i]);
+    dst[i] = df_pack(p.x, p.y);
+  }
+}
+
 // dst = the IEEE doubles of the double-float pairs in src (dst may be src)
 __global__ void k_df_to_ieee(const double* src, double* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -699,6 +708,12 @@ cudaError_t launch_param_grad(int prec, const void* grad, const Grid& g, int kin
 
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st) {
   k_set_int<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ieee_to_df(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_ieee_to_df<<<reduce_blocks() * 8, 256, 0, st>>>(static_cast<const double*>(src),
+                                                    static_cast<double*>(dst), n);
   return cudaGetLastError();
 }
 

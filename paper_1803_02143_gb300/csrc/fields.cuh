@@ -26,6 +26,8 @@ cudaError_t launch_sum_rows(const double* part, int rows, long long cols, double
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 // double-float pairs -> IEEE doubles, n elements (in place when dst == src)
 cudaError_t launch_df_to_ieee(const void* src, void* dst, long long n, cudaStream_t st);
+// the reverse: IEEE doubles to double-float pairs (dst may be src)
+cudaError_t launch_ieee_to_df(const void* src, void* dst, long long n, cudaStream_t st);
 cudaError_t launch_poisson(const PoissonArgs& a, const double* rho, double* E1, double* E2,
                            cudaStream_t st, int* nlaunch);
 cudaError_t launch_poisson_adj(const PoissonArgs& a, const double* Eb1, const double* Eb2,

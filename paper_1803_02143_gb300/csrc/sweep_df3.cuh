@@ -691,8 +691,9 @@ inline size_t ebar_df3_smem(long long D, bool fuse = false, int nbuf = 1) {
 // FUSE: the same CTA then applies the transposed sweep to the staged adjoint
 // tile (forward form on the transposed tables tab2 / tsvec: [B^T; A^T],
 // shifts -s - 1) and writes it back to lam, so the adjoint is read once for
-// both.
-template <int N, bool PERIODIC, bool G_DF, bool FUSE>
+// both.  LAM_DF: lam holds double-float pairs (read, and written by the
+// fused form, in that format; instantiated with G_DF only).
+template <int N, bool PERIODIC, bool G_DF, bool FUSE, bool LAM_DF>
 __global__ void __launch_bounds__(kDf3Threads, N <= 2 ? 3 : 2)
     k_ebar_df3(double* lam, const double* __restrict__ gf,
                double* __restrict__ epart, int ncols, long long rstride, long long ostride, int nc,
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(kDf3Threads, N <= 2 ? 3 : 2)
     if (nbuf == 1) issue(o, tl, tg);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    df3_pair_planar<false>(tl, D * (W / 2));
+    df3_pair_planar<LAM_DF>(tl, D * (W / 2));
     df3_pair_planar<G_DF>(tg, D * (W / 2));
     __syncthreads();
     if (nbuf == 2 && o + (int)gridDim.y < outer)
@@ -816,8 +817,8 @@ __global__ void __launch_bounds__(kDf3Threads, N <= 2 ? 3 : 2)
     }
     if (FUSE && active) {  // the transposed sweep from the staged adjoint, to lam
       const float4* MT = tmat + q * MS;
-      if (ta0 == ta1) df3_run<N, PERIODIC, true, false>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
-      else df3_run<N, PERIODIC, false, false>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
+      if (ta0 == ta1) df3_run<N, PERIODIC, true, LAM_DF>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
+      else df3_run<N, PERIODIC, false, LAM_DF>(tl, MT, c0, cb, ce, ta0, ta1, nc, lam + base, rstride);
     }
     red[g * W + c0] = djoin_fast(ph.x, pl.x);
     red[g * W + c0 + 1] = djoin_fast(ph.y, pl.y);
@@ -853,6 +854,10 @@ cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
   } else {
     return cudaErrorNotSupported;
   }
+  // pair-format adjoints come with pair-format forward inputs; the fused
+  // form writes the adjoint back in its own format
+  if (a.in_df && (!a.g_df || (fuse && !a.out_df))) return cudaErrorNotSupported;
+  if (!a.in_df && fuse && a.out_df) return cudaErrorNotSupported;
   if (ncols != a.key_mod || ((ncols | rstride | ostride) & 1) ||
       ((reinterpret_cast<uintptr_t>(lam) | reinterpret_cast<uintptr_t>(gf)) & 15) ||
       ncols > 0x7fffffffLL - kStridedW || outer > 0x7fffffffLL || D * kStridedW > 0x7fffffffLL)
@@ -866,8 +871,10 @@ cudaError_t launch_ebar_df3_T(const SweepArgs& a, cudaStream_t st) {
   if (gy > 65535) gy = 65535;
   auto pick = [&](auto fuse_t) {
     constexpr bool F = decltype(fuse_t)::value;
-    return a.periodic ? (a.g_df ? k_ebar_df3<N, true, true, F> : k_ebar_df3<N, true, false, F>)
-                      : (a.g_df ? k_ebar_df3<N, false, true, F> : k_ebar_df3<N, false, false, F>);
+    if (a.in_df)
+      return a.periodic ? k_ebar_df3<N, true, true, F, true> : k_ebar_df3<N, false, true, F, true>;
+    return a.periodic ? (a.g_df ? k_ebar_df3<N, true, true, F, false> : k_ebar_df3<N, true, false, F, false>)
+                      : (a.g_df ? k_ebar_df3<N, false, true, F, false> : k_ebar_df3<N, false, false, F, false>);
   };
   auto kfn = fuse ? pick(std::true_type()) : pick(std::false_type());
   cudaError_t e = set_smem(kfn, smem);

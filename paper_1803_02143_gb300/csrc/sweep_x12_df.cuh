@@ -68,14 +68,28 @@ __global__ void __launch_bounds__(kX12DfThreads, N >= 4 ? 4 : 6)
     m2[i] = make_float4(b.x, b.x, b.y, b.y);
   }
   cp_async_wait_all();
-  if (!IN_DF && fold_w) {
-    // the charge-density adjoint folded in: rows += w_v rho_bar(x) (the
-    // operation of k_rho_adj), each thread on the chunks it copied
+  if (fold_w) {
+    // the charge-density adjoint folded in: rows += w_v rho_bar(x), each
+    // thread on the chunks it copied; IEEE rows as k_rho_adj does it, pair
+    // rows by a double-float sum with the split product
     const double w = fold_w[plane];
     const double* r = fold_r + (long long)rank * H * D0;
     for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
-      rows[2 * i] = fma(w, r[2 * i], rows[2 * i]);
-      rows[2 * i + 1] = fma(w, r[2 * i + 1], rows[2 * i + 1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (IN_DF) {
+          const float2 x = df_unpack(rows[2 * i + e]);
+          const float2 t = dsplit(w * r[2 * i + e]);
+          const float sh = x.x + t.x;
+          const float bb = sh - x.x;
+          float sl = (x.x - (sh - bb)) + (t.x - bb);
+          sl += x.y + t.y;
+          const float hh = sh + sl;
+          rows[2 * i + e] = df_pack(hh, sl - (hh - sh));
+        } else {
+          rows[2 * i + e] = fma(w, r[2 * i + e], rows[2 * i + e]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -226,7 +240,6 @@ cudaError_t launch_x12_df_T(const double* f, double* out, const Grid& g, const v
   const long long planes = g.D[2] * g.D[3];
   if (D0 % 2 || ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15))
     return cudaErrorNotSupported;
-  if (fold_w && IN_DF) return cudaErrorInvalidValue;  // the fold adds to IEEE inputs only
   const size_t mats = 2 * (size_t)(2 * N * N) * sizeof(float4);
   // the smallest cluster (2 to 8 CTAs) whose row share fits six CTAs per SM,
   // else the largest that fits one

@@ -134,3 +134,21 @@ def test_backward_weighted_energy_fd(orc, adj_case):
 
     fd = (Jc(f0 + e * dirn) - Jc(f0 - e * dirn)) / (2 * e)
     assert abs(np.sum(grad * dirn) - fd) < 1e-6 * abs(fd) + 1e-12
+
+
+def test_backward_degree0_fd(orc):
+    # Degree 0: each v-sweep is piecewise linear in E, with a kink where E at
+    # an x-node crosses zero (the shift changes its integer part); the
+    # symmetric Landau data has E = 0 at the node of the middle cell of an
+    # odd cell count, so a seeded perturbation of f0 moves E off zero and a
+    # small step (1e-7) keeps the central difference on one side of every
+    # kink.
+    g = orc.Grid(deg=0, nc=(5, 7, 6, 6), lo=LANDAU_LO, hi=LANDAU_HI, dt=0.1)
+    f0 = orc.init(g, orc.LANDAU, [0.5, 0.5, 0.5])
+    f0 = f0 + 1e-3 * random_f(f0.shape, seed=77).reshape(f0.shape)
+    n = 7
+    _, grad, _ = orc.backward(g, f0, n, ckpt=3)
+    dirn = random_f(f0.shape, seed=78).reshape(f0.shape)
+    e = 1e-7
+    fd = (_J(orc, g, f0 + e * dirn, n) - _J(orc, g, f0 - e * dirn, n)) / (2 * e)
+    assert abs(np.sum(grad * dirn) - fd) < 1e-7 * abs(fd)
