@@ -22,10 +22,10 @@ cudaError_t launch_sweep_x12_df(void* f, const Grid& g, const void* ab1, const i
     case 1: return go(std::integral_constant<int, 1>());
     case 2: return go(std::integral_constant<int, 2>());
     case 3: return go(std::integral_constant<int, 3>());
-    // Four nodes per cell (degree 3): the X1 phase's lane stride of two cells
-    // (64 bytes) makes its shared-memory accesses 8-way bank conflicts, and the
-    // fused pass runs slower than the two separate kernels (measured 2.83
-    // against 2.43 ms per pass at 32^4 cells): not supported, the caller runs
+    // Four nodes per cell (degree 3): the pass is bound by its double-float
+    // arithmetic like the two separate kernels, which it does not beat
+    // (2.83 against 2.43 ms per pass at 32^4 cells; 2.39 against 2.33 with
+    // an X1 layout free of bank conflicts): not supported, the caller runs
     // those.
     default: return cudaErrorNotSupported;
   }
