@@ -267,7 +267,10 @@ int sldg_sweep_adjoint(sldg_ctx* ctx, int dim, double frac, void* lam, const voi
 /* Run nsteps Strang steps from the current f like sldg_step while keeping a
  * checkpoint of f every ckpt_every steps in a library-owned device pool
  * (ceil(nsteps / ckpt_every) copies of f), and record W of each step
- * (W_history, host, nullable).  Prepares sldg_backward.
+ * (W_history, host, nullable).  Prepares sldg_backward.  The pool, the W
+ * history and sldg_backward's working copies stay allocated until
+ * sldg_destroy or a recording that needs a larger pool (which releases the
+ * backward's copies first if the pool does not fit beside them).
  * Errors: ARG, OOM (the pool does not fit), UNSUPPORTED (SLDG_FLAG_ORDER4,
  * SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE), CUDA. */
 int sldg_record(sldg_ctx* ctx, int nsteps, int ckpt_every, double* W_history);
@@ -295,7 +298,9 @@ int sldg_objective(sldg_ctx* ctx, const double* cW, int ncW, double* J_out);
  * segment is bisected recursively and its states are recomputed about
  * log2(ckpt_every) times; with one slot, from the checkpoint for every
  * step.  The gradient is the same whatever the number of slots (the same
- * arithmetic, only repeated).
+ * arithmetic, only repeated).  On FP64 storage with double-float sweeps the
+ * adjoint is carried in grad as double-float pairs; the last kernel the call
+ * queues converts it to IEEE doubles.
  * Errors: STATE (no record), BAD_PTR, ARG (ncW differs from the recorded
  * step count), OOM (not even one slot fits), UNSUPPORTED (SLDG_FLAG_ORDER4,
  * SLDG_FLAG_MERGE_DRIFTS or SLDG_FLAG_SPLINE), CUDA. */
