@@ -33,6 +33,7 @@ constexpr int kSplLines = 32;
 constexpr int kSplChunks = 4;
 constexpr int kSplThreads = kSplLines * kSplChunks;
 constexpr int kSplPitch = kSplLines + 1;
+constexpr int kSplRegPts = 32;  // chunk points held in registers (RC)
 
 template <typename T>
 __global__ void k_spline_shifts(long long count, const double* __restrict__ src, double dt,
@@ -55,8 +56,12 @@ __global__ void k_spline_shifts(long long count, const double* __restrict__ src,
 // ...: with NB = 2 the next tile is staged by cp.async into the second
 // input buffer while the current one is computed (NB = 1: each tile is
 // staged after the previous one, the overlap coming from the other CTAs
-// on the SM).
-template <typename T, bool CONTIG, bool KEYCOL, int NB>
+// on the SM).  RC (FP64 chunks of at most kSplRegPts points): a thread keeps its
+// chunk of y in registers from the causal recurrence to the anti-causal
+// one, and across a strided direction (a warp's lanes on 32 consecutive
+// columns) writes the interpolant straight to f, coalesced, instead of
+// through the tile.
+template <typename T, bool CONTIG, bool KEYCOL, int NB, bool RC>
 __global__ void __launch_bounds__(kSplThreads)
     k_spline_sweep(T* __restrict__ f, int n, long long inner, long long outer,
                    long long tiles_per_block, long long ntiles, const T* __restrict__ theta,
@@ -125,6 +130,7 @@ __global__ void __launch_bounds__(kSplThreads)
     // The recurrences run eight points at a time: the eight shared-memory
     // loads of a batch are issued before its chain of dependent FMAs.
     constexpr int B8 = 8;
+    T yr[RC ? kSplRegPts : 1];  // the chunk's y (RC)
     // causal recurrence y_i = u_i - z y_{i-1}: W warm-up points (a multiple
     // of 8) from zero, then the chunk ib .. ie - 1 into Y
     if (act) {
@@ -141,20 +147,38 @@ __global__ void __launch_bounds__(kSplThreads)
 #pragma unroll
         for (int q = 0; q < B8; ++q) y = fma(-z, y, u[q]);
       }
-      int i = ib;
-      for (; i + B8 <= ie; i += B8) {
-        T u[B8];
+      if constexpr (RC) {
+        const int len = ie - ib;
 #pragma unroll
-        for (int q = 0; q < B8; ++q) u[q] = Ul[(i + q) * kSplPitch];
+        for (int q0 = 0; q0 < kSplRegPts; q0 += B8) {
+          T u[B8];
 #pragma unroll
-        for (int q = 0; q < B8; ++q) {
-          y = fma(-z, y, u[q]);
-          Yl[(i + q) * kSplPitch] = y;
+          for (int q = 0; q < B8; ++q)
+            if (q0 + q < len) u[q] = Ul[(ib + q0 + q) * kSplPitch];
+#pragma unroll
+          for (int q = 0; q < B8; ++q)
+            if (q0 + q < len) {
+              y = fma(-z, y, u[q]);
+              yr[q0 + q] = y;
+              Yl[(ib + q0 + q) * kSplPitch] = y;  // for the neighbours' warm-up
+            }
         }
-      }
-      for (; i < ie; ++i) {
-        y = fma(-z, y, Ul[i * kSplPitch]);
-        Yl[i * kSplPitch] = y;
+      } else {
+        int i = ib;
+        for (; i + B8 <= ie; i += B8) {
+          T u[B8];
+#pragma unroll
+          for (int q = 0; q < B8; ++q) u[q] = Ul[(i + q) * kSplPitch];
+#pragma unroll
+          for (int q = 0; q < B8; ++q) {
+            y = fma(-z, y, u[q]);
+            Yl[(i + q) * kSplPitch] = y;
+          }
+        }
+        for (; i < ie; ++i) {
+          y = fma(-z, y, Ul[i * kSplPitch]);
+          Yl[i * kSplPitch] = y;
+        }
       }
     }
     __syncthreads();
@@ -173,20 +197,30 @@ __global__ void __launch_bounds__(kSplThreads)
         for (int q = 0; q < B8; ++q) v = fma(-z, v, u[q]);
       }
       const T sz = T(6) * z;
-      int i = ie - 1;
-      for (; i - B8 + 1 >= ib; i -= B8) {
-        T u[B8];
+      if constexpr (RC) {
+        const int len = ie - ib;
 #pragma unroll
-        for (int q = 0; q < B8; ++q) u[q] = Yl[(i - q) * kSplPitch];
+        for (int q = kSplRegPts - 1; q >= 0; --q)
+          if (q < len) {
+            v = fma(-z, v, yr[q]);
+            Ul[(ib + q) * kSplPitch] = sz * v;
+          }
+      } else {
+        int i = ie - 1;
+        for (; i - B8 + 1 >= ib; i -= B8) {
+          T u[B8];
 #pragma unroll
-        for (int q = 0; q < B8; ++q) {
-          v = fma(-z, v, u[q]);
-          Ul[(i - q) * kSplPitch] = sz * v;
+          for (int q = 0; q < B8; ++q) u[q] = Yl[(i - q) * kSplPitch];
+#pragma unroll
+          for (int q = 0; q < B8; ++q) {
+            v = fma(-z, v, u[q]);
+            Ul[(i - q) * kSplPitch] = sz * v;
+          }
         }
-      }
-      for (; i >= ib; --i) {
-        v = fma(-z, v, Yl[i * kSplPitch]);
-        Ul[i * kSplPitch] = sz * v;
+        for (; i >= ib; --i) {
+          v = fma(-z, v, Yl[i * kSplPitch]);
+          Ul[i * kSplPitch] = sz * v;
+        }
       }
     }
     __syncthreads();
@@ -201,6 +235,10 @@ __global__ void __launch_bounds__(kSplThreads)
       const T w1 = (T(4) - T(6) * om * om + T(3) * om * om * om) * sixth;
       const T w2 = (T(4) - T(6) * th * th + T(3) * th * th * th) * sixth;
       const T w3 = om * om * om * sixth;
+      // output point i: the tile's Y, or (RC across a strided direction) f
+      constexpr bool DIRECT = RC && !CONTIG;
+      T* const orow = DIRECT ? base_of(x) + l : Yl;
+      const long long ostr = DIRECT ? inner : kSplPitch;
       int k = (ib - s - 2) % n;
       if (k < 0) k += n;
       T c0 = Ul[k * kSplPitch];
@@ -219,7 +257,7 @@ __global__ void __launch_bounds__(kSplThreads)
         }
 #pragma unroll
         for (int q = 0; q < B8; ++q) {
-          Yl[(i + q) * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * u[q])));
+          orow[(i + q) * ostr] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * u[q])));
           c0 = c1;
           c1 = c2;
           c2 = u[q];
@@ -228,13 +266,14 @@ __global__ void __launch_bounds__(kSplThreads)
       for (; i < ie; ++i) {
         const T c3 = Ul[k * kSplPitch];
         k = k + 1 == n ? 0 : k + 1;
-        Yl[i * kSplPitch] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * c3)));
+        orow[i * ostr] = fma(w0, c0, fma(w1, c1, fma(w2, c2, w3 * c3)));
         c0 = c1;
         c1 = c2;
         c2 = c3;
       }
     }
-    __syncthreads();
+    __syncthreads();  // (the next tile may then be staged into U)
+    if (RC && !CONTIG) continue;  // written by the evaluation
     T* base = base_of(x);
     if (CONTIG) {
       for (int ll = warp; ll < x.nl; ll += kWarps) {
@@ -259,7 +298,12 @@ cudaError_t launch_spline_T(const SweepArgs& a, cudaStream_t st) {
   // v-sweep and 4.88 against 5.12 ms per FP64 v-sweep at 128^4 points
   const int nb = 8 * (3 * buf + 1024) <= 228 * 1024 ? 2 : 1;
   const size_t smem = (nb + 1) * buf;
-  auto kfn = nb == 2 ? k_spline_sweep<T, CONTIG, KEYCOL, 2> : k_spline_sweep<T, CONTIG, KEYCOL, 1>;
+  // FP64 chunks of at most kSplRegPts points stay in registers (at 128^4
+  // points 4.71 against 4.87 ms per v-sweep, 9.49 against 10.11 per pair of
+  // x1 sweeps); FP32 gains nothing from it (0.578 against 0.573 ms)
+  const bool rc = sizeof(T) == 8 && (n + kSplChunks - 1) / kSplChunks <= kSplRegPts;
+  auto kfn = nb == 2 ? (rc ? k_spline_sweep<T, CONTIG, KEYCOL, 2, true> : k_spline_sweep<T, CONTIG, KEYCOL, 2, false>)
+                     : (rc ? k_spline_sweep<T, CONTIG, KEYCOL, 1, true> : k_spline_sweep<T, CONTIG, KEYCOL, 1, false>);
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
