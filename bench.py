@@ -229,10 +229,11 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
 
 # translation unit of each kernel family (its sources key the traffic entry)
 # (workload, precision, kind) whose launches run another kernel than the
-# capture case: FP32 v-sweeps of 384-value lines exceed the packed tile and
-# run the one-lane kernel, while the 48-value lines of the capture run the
-# packed one
-NCU_NOT_SCALED = {("two_stream_64x128", "fp32", "v1"), ("two_stream_64x128", "fp32", "v2")}
+# capture case: FP32 v-sweeps of 384- and 256-value lines exceed the packed
+# tile and run the one-lane kernel, while the 48- and 32-value lines of the
+# capture cases run the packed one
+NCU_NOT_SCALED = {("two_stream_64x128", "fp32", "v1"), ("two_stream_64x128", "fp32", "v2"),
+                  ("mixed_landau_128", "fp32", "v1"), ("mixed_landau_128", "fp32", "v2")}
 
 KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df_x12.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
                 ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),

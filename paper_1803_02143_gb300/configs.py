@@ -90,6 +90,13 @@ WORKLOADS = {
     # mixed precision forward+adjoint, 128^4 cells, degree 1 (4.3e9 dofs), fp32 f
     "mixed_landau_128": Workload("mixed_landau_128", _landau(1, 128, 0.05, 0.5, "fp32"),
                                  N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 200, ckpt=25),
+    # its x-planes and x-lines (128^2 x-cells, degree 1) over 16^2 v-cells:
+    # 6.7e7 dofs, 268 MB in FP32 (beyond L2), the profiling case of that grid
+    "mixed_landau_128x16": Workload(
+        "mixed_landau_128x16",
+        Config(degree=1, ncell=(128, 128, 16, 16), lo=LANDAU_LO, hi=LANDAU_HI, dt=0.05,
+               precision="fp32"),
+        N.SLDG_INIT_LANDAU, (0.5, 0.5, 0.5), 200),
 }
 
 
