@@ -1302,12 +1302,6 @@ int sldg_backward_stats(const sldg_ctx* c, long long* recomputed_steps, int* slo
 
 namespace {
 
-// Adjoint of Strang step m (global index) from its forward intermediates g2
-// (input of V1) and g3 (input of V2) and its kick field (E: 2 D_0 D_1
-// doubles, or null when the context's field is already the step's):
-// grad <- (step m)^T grad + the dJ/dW_m c_m contributions (Eq. AB-sldg
-// transposed, the v-shift derivatives, the Poisson and charge-density
-// adjoints).
 // The backward keeps the adjoint in double-float pairs on FP64 storage with
 // double-float sweeps (no conversion through the FP64 pipe in its passes);
 // sldg_backward converts the gradient to IEEE doubles at the end.
@@ -1339,6 +1333,12 @@ int adjoint_drift(sldg_ctx* c, void* lam, bool rho_fold = false) {
   return SLDG_OK;
 }
 
+// Adjoint of Strang step m (global index) from its forward intermediates g2
+// (input of V1) and g3 (input of V2) and its kick field (E: 2 D_0 D_1
+// doubles, or null when the context's field is already the step's):
+// grad <- (step m)^T grad + the dJ/dW_m c_m contributions (Eq. AB-sldg
+// transposed, the v-shift derivatives, the Poisson and charge-density
+// adjoints).
 int adjoint_step_from(sldg_ctx* c, const void* g2, const void* g3, const double* E, int m,
                       const double* cW, void* grad) {
   const Grid& g = c->g;
