@@ -112,15 +112,26 @@ def test_mass_conserved_with_periodic_v(orc):
 
 
 def test_nonlinear_landau_energy_error_band(orc):
-    # Sec. 4: energy error of order 1e-3 after the transient at tau = 0.1
-    # (on this coarse grid the spatial error adds to it: within 20x the order).
+    # Sec. 4: at tau = 0.1 the relative error in the total energy is of order
+    # 1e-3 after the transient and comes from the time integration: within a
+    # factor 3 of that order here (6.2e-4 on this grid, the same to 2% on
+    # grids up to 16^2 x 24^2 cells), and halving tau over the same time span
+    # divides it by about 4 (the second order of Strang splitting; a
+    # spatial error would not shrink with tau).
     ref = golden_kv("nonlinear_landau_energy_error.txt")
-    g = _grid(orc, 2, (8, 8, 16, 16), dt=ref["tau"])
-    f0 = orc.init(g, orc.LANDAU, [ref["eps"], ref["k"], ref["k"]])
-    _, E1, E2 = orc.fields(g, f0)
-    d0 = orc.diagnostics(g, f0, E1, E2)
-    f, _, _, _ = orc.step(g, f0, 40)
-    _, E1, E2 = orc.fields(g, f)
-    d1 = orc.diagnostics(g, f, E1, E2)
-    err = abs(d1["total"] - d0["total"]) / d0["total"]
-    assert err < 20 * ref["energy_error_order"], err
+
+    def energy_error(tau, nsteps):
+        g = _grid(orc, 2, (8, 8, 16, 16), dt=tau)
+        f0 = orc.init(g, orc.LANDAU, [ref["eps"], ref["k"], ref["k"]])
+        _, E1, E2 = orc.fields(g, f0)
+        d0 = orc.diagnostics(g, f0, E1, E2)
+        f, _, _, _ = orc.step(g, f0, nsteps)
+        _, E1, E2 = orc.fields(g, f)
+        d1 = orc.diagnostics(g, f, E1, E2)
+        return abs(d1["total"] - d0["total"]) / d0["total"]
+
+    err = energy_error(ref["tau"], 40)
+    order = ref["energy_error_order"]
+    assert order / 3 < err < 3 * order, err
+    ratio = energy_error(ref["tau"] / 2, 80) / err
+    assert 1 / 5 < ratio < 1 / 3, ratio
