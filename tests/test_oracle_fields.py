@@ -38,6 +38,36 @@ def test_poisson_single_mode_closed_form(orc, m, deg):
     np.testing.assert_allclose(E2, eps * k[1] * m[1] * np.sin(ph) / km2, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("deg", [1, 2, 3])
+@pytest.mark.parametrize("mp", [7, 9, 11])
+@pytest.mark.parametrize("d", [0, 1])
+def test_poisson_high_mode_aliasing_exact(orc, deg, mp, d):
+    # With the default cap K = nc - 1 a high mode m' aliases onto nc - m'.
+    # The node set repeats every cell, so the composite Gauss-Legendre sum of
+    # exp(i kappa j x) over the box vanishes unless j is a multiple of nc, and
+    # for j = +-nc it is L times a = -1/2 sum_n w_n cos(pi t_n) (the one-cell
+    # rule's error on one period; nodes t_n, weights w_n from numpy).  For
+    # rho - 1 = eps cos(kappa m' x_d) that gives rho_hat(+-m') = eps/2 and
+    # rho_hat(+-(nc - m')) = a eps/2, hence exactly
+    #   E_d = eps sin(kappa m' x)/(kappa m') + a eps sin(kappa m_a x)/(kappa m_a),
+    # m_a = nc - m', and no field in the other component.
+    lo = (0.0, 0.0, -6.0, -6.0)
+    hi = (4 * np.pi, 6 * np.pi, 6.0, 6.0)
+    nc = (12, 12, 2, 2)
+    g = _grid(orc, deg=deg, nc=nc, lo=lo, hi=hi)
+    kap = 2 * np.pi / (hi[d] - lo[d])
+    X2, X1 = np.meshgrid(g.nodes(1), g.nodes(0), indexing="ij")
+    X = X1 if d == 0 else X2
+    eps = 0.3
+    E = orc.poisson(g, 1 + eps * np.cos(kap * mp * X))
+    t, w = np.polynomial.legendre.leggauss(deg + 1)
+    a = -0.5 * np.sum(w * np.cos(np.pi * t))
+    ma = nc[d] - mp
+    pred = eps * (np.sin(kap * mp * X) / (kap * mp) + a * np.sin(kap * ma * X) / (kap * ma))
+    np.testing.assert_allclose(E[d], pred, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(E[1 - d], 0, atol=1e-13)
+
+
 def test_poisson_landau_field_default_modes(orc):
     # Landau density 1 + eps cos(k x1) at degree 3 with the default mode
     # count: E1 = (eps/k) sin(k x1), E2 = 0, up to the aliasing of the
