@@ -227,7 +227,6 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
                "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active,"
                "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active")
 
-# translation unit of each kernel family (its sources key the traffic entry)
 # (workload, precision, kind) whose launches run another kernel than the
 # capture case: FP32 v-sweeps of 384- and 256-value lines exceed the packed
 # tile and run the one-lane kernel, while the 48- and 32-value lines of the
@@ -235,6 +234,7 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
 NCU_NOT_SCALED = {("two_stream_64x128", "fp32", "v1"), ("two_stream_64x128", "fp32", "v2"),
                   ("mixed_landau_128", "fp32", "v1"), ("mixed_landau_128", "fp32", "v2")}
 
+# translation unit of each kernel family (its sources key the traffic entry)
 KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df_x12.cu"), ("k_sweep_strided_df3", "sweep_df.cu"),
                 ("k_sweep_x1_warp", "sweep_df.cu"), ("k_sweep_x12_f32", "sweep_f32.cu"),
                 ("k_sweep_strided_f2", "sweep_f32.cu"), ("k_sweep_x1_f2warp", "sweep_f32.cu"),
@@ -242,9 +242,13 @@ KERNEL_UNITS = (("k_sweep_x12_df", "sweep_df_x12.cu"), ("k_sweep_strided_df3", "
 
 
 def _kernel_kind(name):
-    """(kind, precision) of a sweep kernel from its ncu name, or None."""
+    """(kind, precision) of a sweep kernel from its ncu name, or None.  FP64:
+    the double-float families (a `_df` in the name, and the four-node x1
+    kernel `k_sweep_x1_warp`) and kernels whose first template argument is
+    double (`k_rho_partial<T>`, `k_spline_sweep<T>`)."""
     base = name.split("(")[0]  # template arguments only, not the parameter list
-    prec = "fp64" if ("_df" in base or "double" in base) else "fp32"
+    fp64 = "_df" in base or "k_sweep_x1_warp" in base or re.search(r"<\s*double\b", base)
+    prec = "fp64" if fp64 else "fp32"
     if "k_sweep_x12" in name:
         return "x12", prec
     if "k_sweep_x1" in name:
@@ -252,7 +256,7 @@ def _kernel_kind(name):
     if "k_rho_partial" in name:
         return "rho", prec
     m = re.search(r"k_spline_sweep<\s*\w+,\s*(\w+),\s*(\w+)", name)
-    if m:  # <T, CONTIG, KEYCOL, NB>: x1 lines contiguous, v-sweeps keyed by column
+    if m:  # <T, CONTIG, KEYCOL, NB, RC>: x1 lines contiguous, v-sweeps keyed by column
         if m.group(1) in ("1", "true"):
             return "x1", prec
         return ("v", prec) if m.group(2) in ("1", "true") else ("x2", prec)
