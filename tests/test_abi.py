@@ -111,11 +111,33 @@ def test_rho_noalloc_rejects_what_init_rejects(lib, bad):
 
 
 def test_null_context_is_rejected(lib):
+    # every entry point that takes a context returns SLDG_ERR_BAD_PTR for a
+    # null one (the counters 0, destroy nothing) before it touches any other
+    # argument or the device; the other pointers are non-null stand-ins of
+    # their declared types, never dereferenced
     from paper_1803_02143_gb300 import _native as N
 
-    assert lib.sldg_step(None, 1, None) == N.SLDG_ERR_BAD_PTR
-    assert lib.sldg_sweep(None, 0, 0.5) == N.SLDG_ERR_BAD_PTR
+    def standin(t):
+        if t is ctypes.c_void_p:
+            return ctypes.c_void_p(256)
+        if isinstance(t, type) and issubclass(t, ctypes._Pointer):
+            return ctypes.cast(ctypes.c_void_p(256), t)
+        if t is ctypes.c_double:
+            return 0.5
+        return 1
+
+    names = ["sldg_bind", "sldg_set_initial", "sldg_get_f", "sldg_set_f", "sldg_step",
+             "sldg_step_host_batches", "sldg_sweep", "sldg_drift", "sldg_compute_fields",
+             "sldg_set_field", "sldg_fields", "sldg_diagnostics", "sldg_sweep_adjoint",
+             "sldg_record", "sldg_objective", "sldg_backward", "sldg_set_slot_limit",
+             "sldg_backward_stats", "sldg_initial_param_grad", "sldg_x_pass_shape",
+             "sldg_timing", "sldg_timing_read"]
+    for name in names:
+        fn = getattr(lib, name)
+        args = [None] + [standin(t) for t in fn.argtypes[1:]]
+        assert fn(*args) == N.SLDG_ERR_BAD_PTR, name
     assert lib.sldg_numel(None) == 0
+    assert lib.sldg_launch_count(None) == 0
     lib.sldg_destroy(None)
 
 
